@@ -1,0 +1,466 @@
+/*
+ * Plain FP64 CPU oracle for the Blast beyond-Limber angular power spectrum
+ * (Chiarenza, Bonici, Percival, White, arXiv:2410.03632).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the benchmark's
+ * CPU-baseline leg load this file's shared library; the product library never
+ * does, and this file shares no code, header, table or constant generator with
+ * the CUDA path.  Everything is IEEE double, round to nearest, written as the
+ * plain definition of each step with no blocking or fusion beyond loop order.
+ *
+ * Steps, in the paper's order and notation:
+ *   grids        Sec. 3.2: Simpson in chi, first-kind Chebyshev points with
+ *                Clenshaw-Curtis-type (Fejer 1) weights in R, Clenshaw-Curtis in k
+ *                (App. C); Chebyshev points for the fit (Eq. chebpoints).
+ *   j_l(x)       spherical Bessel functions of Eq. cls-general.
+ *   T~           basis integrals, Eq. t_tilde, f^gg = k^2, f^ss = 1/k^2, f^gs = 1.
+ *   c_n          interpolation coefficients at Chebyshev points (Eq. a2), obtained
+ *                from the samples by the discrete cosine transform that Eq. dft
+ *                stands for.
+ *   w_l          projected matter density, Eq. pmd, with c_n(chi1,chi2) =
+ *                D(chi1) D(chi2) a_n (growth-separable P, Sec. 4.2.1).
+ *   C_l          chi-R quadrature of Eq. final_cls in its unsymmetrised form
+ *                (first line of Eq. app1 with chi2 = R chi1), times the probe
+ *                prefactor N(l) of Eqs. gg, ss, gs.
+ *
+ * Status: every function returns 0 on success and a negative value on bad input.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846264338327950288
+
+static int orc_threads(int nthreads)
+{
+#ifdef _OPENMP
+    return nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* Grids (Sec. 3.2)                                                          */
+/* ------------------------------------------------------------------------- */
+
+/* X evenly spaced chi nodes on [lo, hi] with composite Simpson weights.  For an
+ * odd number of intervals the last three intervals take Simpson's 3/8 rule. */
+int orc_chi_grid(int X, double lo, double hi, double *chi, double *w)
+{
+    if (X < 3 || (X % 2 == 0 && X < 4) || !(hi > lo)) return -1;
+    double h = (hi - lo) / (double)(X - 1);
+    for (int a = 0; a < X; a++) { chi[a] = lo + h * (double)a; w[a] = 0.0; }
+    int n13 = (X % 2 == 1) ? X - 1 : X - 4; /* intervals under the 1/3 rule */
+    for (int i = 0; i < n13; i += 2) {
+        w[i] += h / 3.0; w[i + 1] += 4.0 * h / 3.0; w[i + 2] += h / 3.0;
+    }
+    if (X % 2 == 0) {
+        int s = X - 4;
+        w[s] += 3.0 * h / 8.0; w[s + 1] += 9.0 * h / 8.0;
+        w[s + 2] += 9.0 * h / 8.0; w[s + 3] += 3.0 * h / 8.0;
+    }
+    return 0;
+}
+
+/* Fejer first rule on [-1,1]: the n first-kind Chebyshev points
+ * x_k = cos((2k+1) pi / 2n) of Eq. chebpoints and the weights that integrate
+ * every polynomial of degree < n exactly.  Output ordered by increasing x. */
+static void orc_fejer1(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; i++) {
+        int k = n - 1 - i; /* increasing x */
+        double th = ORC_PI * (2.0 * k + 1.0) / (2.0 * n);
+        double s = 0.0;
+        for (int j = 1; j <= n / 2; j++)
+            s += cos(2.0 * j * th) / (4.0 * (double)j * j - 1.0);
+        x[i] = cos(th);
+        w[i] = (2.0 / n) * (1.0 - 2.0 * s);
+    }
+}
+
+/* R nodes: two panels [lo, 1] and [1, hi], each holding Rn/2 first-kind
+ * Chebyshev points with Fejer-1 weights, so that nodes crowd towards R = 1 from
+ * both sides (the diagonal chi1 = chi2 that dominates the integral, App. A). */
+int orc_R_grid(int Rn, double lo, double hi, double *R, double *w)
+{
+    if (Rn < 2 || Rn % 2 != 0 || !(lo > 0.0) || !(lo < 1.0) || !(hi > 1.0)) return -1;
+    int n = Rn / 2;
+    double *x = (double *)malloc(sizeof(double) * n), *wx = (double *)malloc(sizeof(double) * n);
+    if (!x || !wx) { free(x); free(wx); return -2; }
+    orc_fejer1(n, x, wx);
+    double c1 = 0.5 * (lo + 1.0), h1 = 0.5 * (1.0 - lo);
+    double c2 = 0.5 * (1.0 + hi), h2 = 0.5 * (hi - 1.0);
+    for (int i = 0; i < n; i++) {
+        R[i] = c1 + h1 * x[i];         w[i] = h1 * wx[i];
+        R[n + i] = c2 + h2 * x[i];     w[n + i] = h2 * wx[i];
+    }
+    free(x); free(wx);
+    return 0;
+}
+
+/* Clenshaw-Curtis rule with Nk = n+1 points (n even) on [kmin, kmax] (Sec. 3.2,
+ * App. C): x_m = cos(m pi / n), k_m = (kmin+kmax)/2 + (kmax-kmin)/2 x_m, and
+ * w_m = (c_m/n) [1 - sum_{j=1}^{n/2} b_j cos(2 j m pi / n) / (4 j^2 - 1)] times
+ * (kmax-kmin)/2, with c_0 = c_n = 1, c_m = 2 otherwise, b_{n/2} = 1, b_j = 2
+ * otherwise.  Every cosine argument is reduced exactly in integers, 2 pi (j m
+ * mod n) / n, and read from a table of cos(2 pi p / n). */
+int orc_cc_grid(int Nk, double kmin, double kmax, double *k, double *x, double *w, int nthreads)
+{
+    if (Nk < 3 || (Nk - 1) % 2 != 0 || !(kmax > kmin)) return -1;
+    int n = Nk - 1;
+    double *tab = (double *)malloc(sizeof(double) * n);
+    if (!tab) return -2;
+    for (int p = 0; p < n; p++) tab[p] = cos(2.0 * ORC_PI * (double)p / (double)n);
+    double kc = 0.5 * (kmin + kmax), kh = 0.5 * (kmax - kmin);
+    int nt = orc_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+    for (int m = 0; m <= n; m++) {
+        double s = 0.0;
+        for (int j = 1; j <= n / 2; j++) {
+            double b = (j == n / 2) ? 1.0 : 2.0;
+            int64_t p = ((int64_t)j * (int64_t)m) % (int64_t)n;
+            s += b * tab[p] / (4.0 * (double)j * (double)j - 1.0);
+        }
+        double c = (m == 0 || m == n) ? 1.0 : 2.0;
+        /* x_m = cos(m pi / n) = cos(2 pi m / (2n)) */
+        double xm = cos(ORC_PI * (double)m / (double)n);
+        x[m] = xm;
+        k[m] = kc + kh * xm;
+        w[m] = kh * (c / (double)n) * (1.0 - s);
+    }
+    free(tab);
+    return 0;
+}
+
+/* Map between k in [kmin, kmax] and the Chebyshev variable in [-1, 1]:
+ * kmap 0 is linear in k, kmap 1 is linear in ln k. */
+static double orc_k_to_x(int kmap, double k, double kmin, double kmax)
+{
+    double x = (kmap == 0) ? (2.0 * k - kmin - kmax) / (kmax - kmin)
+                           : 2.0 * (log(k) - log(kmin)) / (log(kmax) - log(kmin)) - 1.0;
+    return x > 1.0 ? 1.0 : (x < -1.0 ? -1.0 : x);
+}
+
+static double orc_x_to_k(int kmap, double x, double kmin, double kmax)
+{
+    if (kmap == 0) return 0.5 * (kmin + kmax) + 0.5 * (kmax - kmin) * x;
+    return exp(log(kmin) + 0.5 * (log(kmax) - log(kmin)) * (x + 1.0));
+}
+
+/* Eq. chebpoints: t_j = cos((2j+1) pi / 2N), j < N, and the k they map to. */
+int orc_cheb_knodes(int N, double kmin, double kmax, int kmap, double *t, double *k)
+{
+    if (N < 1 || !(kmax > kmin) || kmap < 0 || kmap > 1 || (kmap == 1 && !(kmin > 0.0))) return -1;
+    for (int j = 0; j < N; j++) {
+        t[j] = cos(ORC_PI * (2.0 * j + 1.0) / (2.0 * N));
+        k[j] = orc_x_to_k(kmap, t[j], kmin, kmax);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Spherical Bessel functions j_0 .. j_lmax at one argument x >= 0.           */
+/* For x > lmax the forward recurrence j_{l+1} = (2l+1)/x j_l - j_{l-1} from   */
+/* j_0 = sin x / x, j_1 = sin x / x^2 - cos x / x is stable.  Otherwise        */
+/* Miller's backward recurrence runs from l0 = lmax + 20 + sqrt(40 lmax) with  */
+/* arbitrary start values and is normalised by the addition-theorem sum rule   */
+/* sum_l (2l+1) j_l(x)^2 = 1, with the sign taken from j_0 (or j_1).          */
+/* ------------------------------------------------------------------------- */
+int orc_jl(int lmax, double x, double *j)
+{
+    if (lmax < 0 || !(x >= 0.0) || isinf(x)) return -1;
+    if (x == 0.0) {
+        j[0] = 1.0;
+        for (int l = 1; l <= lmax; l++) j[l] = 0.0;
+        return 0;
+    }
+    double s = sin(x), c = cos(x);
+    double j0 = s / x;
+    if (lmax == 0) { j[0] = j0; return 0; }
+    if (x > (double)lmax) {
+        j[0] = j0;
+        j[1] = s / (x * x) - c / x;
+        for (int l = 1; l < lmax; l++) j[l + 1] = (2.0 * l + 1.0) / x * j[l] - j[l - 1];
+        return 0;
+    }
+    int l0 = lmax + 20 + (int)sqrt(40.0 * (double)lmax);
+    double fp1 = 0.0, f = 1.0, sum = 0.0;
+    for (int l = l0; l >= 1; l--) {
+        if (l <= lmax) j[l] = f;
+        sum += (2.0 * l + 1.0) * f * f;
+        double fm1 = (2.0 * l + 1.0) / x * f - fp1;
+        fp1 = f;
+        f = fm1;
+        if (fabs(f) > 1e120) {
+            f *= 1e-120; fp1 *= 1e-120; sum *= 1e-240;
+            for (int m = l; m <= lmax; m++) j[m] *= 1e-120;
+        }
+    }
+    j[0] = f;
+    sum += f * f;
+    double norm = 1.0 / sqrt(sum);
+    /* sign: from whichever of j_0, j_1 is larger in magnitude */
+    double j1 = (x < 1e-3) ? x / 3.0 * (1.0 - x * x / 10.0) : (s / (x * x) - c / x);
+    double sg;
+    if (fabs(j0) >= fabs(j1)) sg = ((j0 >= 0.0) == (j[0] >= 0.0)) ? 1.0 : -1.0;
+    else sg = ((j1 >= 0.0) == (j[1] >= 0.0)) ? 1.0 : -1.0;
+    for (int l = 0; l <= lmax; l++) j[l] *= sg * norm;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Basis integrals, Eq. t_tilde:                                             */
+/*   T~^{AB}_{n;l}(chi1, chi2) = int_{kmin}^{kmax} dk f^{AB}(k) T_n(x(k))      */
+/*                                 j_l(k chi1) j_l(k chi2)                    */
+/* with x(k) the map of [kmin, kmax] onto [-1, 1] (linear in k or in ln k),  */
+/* evaluated with the                                                         */
+/* Clenshaw-Curtis rule of Sec. 3.2 and Neumaier-compensated sums.            */
+/* Types: 0 = gg (f = k^2), 1 = gs (f = 1), 2 = ss (f = 1/k^2).              */
+/* Output T[t][e][n][q] for the ells ell[0..n_ell) and point pairs            */
+/* (chi1[q], chi2[q]), q < nq.                                               */
+/* ------------------------------------------------------------------------- */
+int orc_basis(int n_ell, const int *ell, int nq, const double *chi1, const double *chi2,
+              int N, double kmin, double kmax, int kmap, int Nk, int nthreads, double *T)
+{
+    if (n_ell < 1 || nq < 1 || N < 1 || !(kmin > 0.0) || kmap < 0 || kmap > 1) return -1;
+    int lmax = 0;
+    for (int e = 0; e < n_ell; e++) {
+        if (ell[e] < 0) return -1;
+        if (ell[e] > lmax) lmax = ell[e];
+    }
+    double *k = (double *)malloc(sizeof(double) * Nk);
+    double *x = (double *)malloc(sizeof(double) * Nk);
+    double *w = (double *)malloc(sizeof(double) * Nk);
+    double *A = (double *)malloc(sizeof(double) * (size_t)Nk * 3 * N);
+    if (!k || !x || !w || !A) { free(k); free(x); free(w); free(A); return -2; }
+    int rc = orc_cc_grid(Nk, kmin, kmax, k, x, w, nthreads);
+    if (rc) { free(k); free(x); free(w); free(A); return rc; }
+    /* A[m][t][n] = w_m f_t(k_m) T_n(x_m), T_n by the three-term recurrence */
+    for (int m = 0; m < Nk; m++) {
+        double f[3] = {k[m] * k[m], 1.0, 1.0 / (k[m] * k[m])};
+        double xc = orc_k_to_x(kmap, k[m], kmin, kmax);
+        double tm1 = 1.0, tn = xc;
+        for (int n = 0; n < N; n++) {
+            double Tn;
+            if (n == 0) Tn = 1.0;
+            else if (n == 1) Tn = xc;
+            else { Tn = 2.0 * xc * tn - tm1; tm1 = tn; tn = Tn; }
+            for (int t = 0; t < 3; t++) A[((size_t)m * 3 + t) * N + n] = w[m] * f[t] * Tn;
+        }
+    }
+    const size_t per_q = (size_t)3 * n_ell * N;
+    int nt = orc_threads(nthreads);
+    int fail = 0;
+#pragma omp parallel num_threads(nt)
+    {
+        double *acc = (double *)calloc(per_q, sizeof(double));
+        double *cmp = (double *)calloc(per_q, sizeof(double));
+        double *b1 = (double *)malloc(sizeof(double) * (lmax + 1));
+        double *b2 = (double *)malloc(sizeof(double) * (lmax + 1));
+        double *bm = (double *)malloc(sizeof(double) * n_ell);
+        if (!acc || !cmp || !b1 || !b2 || !bm) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 1)
+        for (int q = 0; q < nq; q++) {
+            if (fail) continue;
+            memset(acc, 0, per_q * sizeof(double));
+            memset(cmp, 0, per_q * sizeof(double));
+            for (int m = 0; m < Nk; m++) {
+                orc_jl(lmax, k[m] * chi1[q], b1);
+                orc_jl(lmax, k[m] * chi2[q], b2);
+                for (int e = 0; e < n_ell; e++) bm[e] = b1[ell[e]] * b2[ell[e]];
+                for (int t = 0; t < 3; t++) {
+                    const double *Am = A + ((size_t)m * 3 + t) * N;
+                    for (int e = 0; e < n_ell; e++) {
+                        double v = bm[e];
+                        double *s = acc + ((size_t)t * n_ell + e) * N;
+                        double *c = cmp + ((size_t)t * n_ell + e) * N;
+                        for (int n = 0; n < N; n++) {
+                            double term = Am[n] * v;
+                            double tsum = s[n] + term;
+                            c[n] += (fabs(s[n]) >= fabs(term)) ? ((s[n] - tsum) + term)
+                                                              : ((term - tsum) + s[n]);
+                            s[n] = tsum;
+                        }
+                    }
+                }
+            }
+            for (size_t i = 0; i < per_q; i++) T[i * (size_t)nq + q] = acc[i] + cmp[i];
+        }
+        free(acc); free(cmp); free(b1); free(b2); free(bm);
+    }
+    free(k); free(x); free(w); free(A);
+    return fail ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Chebyshev interpolation coefficients (Eqs. chebpoints, a2, dft)           */
+/* ------------------------------------------------------------------------- */
+
+/* Coefficients c_n of the degree-(N-1) interpolant through the samples
+ * vals[j] = f(t_j) at the first-kind points t_j = cos((2j+1) pi / 2N):
+ *   c_0 = (1/N) sum_j f(t_j),  c_n = (2/N) sum_j f(t_j) cos(n (2j+1) pi / 2N).
+ * Cosine arguments are reduced exactly: n (2j+1) mod 4N. */
+int orc_cheb_dct(int N, const double *vals, double *a)
+{
+    if (N < 1) return -1;
+    double *tab = (double *)malloc(sizeof(double) * 4 * N);
+    if (!tab) return -2;
+    for (int p = 0; p < 4 * N; p++) tab[p] = cos(ORC_PI * (double)p / (2.0 * N));
+    for (int n = 0; n < N; n++) {
+        double s = 0.0;
+        for (int j = 0; j < N; j++) s += vals[j] * tab[((long)n * (2 * j + 1)) % (4 * N)];
+        a[n] = (n == 0 ? 1.0 : 2.0) * s / (double)N;
+    }
+    free(tab);
+    return 0;
+}
+
+/* Natural cubic spline through (u_i, v_i), i < n, u strictly increasing,
+ * evaluated at uq[0..m).  Second derivatives from the tridiagonal system by the
+ * Thomas algorithm; a query outside [u_0, u_{n-1}] is an error. */
+int orc_spline_natural(int n, const double *u, const double *v, int m, const double *uq, double *out)
+{
+    if (n < 3 || m < 0) return -1;
+    for (int i = 1; i < n; i++) if (!(u[i] > u[i - 1])) return -1;
+    double *M = (double *)calloc(n, sizeof(double));
+    double *cp = (double *)calloc(n, sizeof(double));
+    double *dp = (double *)calloc(n, sizeof(double));
+    if (!M || !cp || !dp) { free(M); free(cp); free(dp); return -2; }
+    /* unknowns M_1..M_{n-2}; row i: h_{i-1} M_{i-1} + 2(h_{i-1}+h_i) M_i + h_i M_{i+1} = r_i */
+    for (int i = 1; i <= n - 2; i++) {
+        double hl = u[i] - u[i - 1], hr = u[i + 1] - u[i];
+        double r = 6.0 * ((v[i + 1] - v[i]) / hr - (v[i] - v[i - 1]) / hl);
+        double b = 2.0 * (hl + hr);
+        double lo = (i > 1) ? hl : 0.0;
+        double den = b - lo * cp[i - 1];
+        cp[i] = hr / den;
+        dp[i] = (r - lo * dp[i - 1]) / den;
+    }
+    M[n - 1] = 0.0;
+    for (int i = n - 2; i >= 1; i--) M[i] = dp[i] - cp[i] * M[i + 1];
+    M[0] = 0.0;
+    int rc = 0;
+    for (int q = 0; q < m; q++) {
+        double x = uq[q];
+        if (!(x >= u[0] && x <= u[n - 1])) { rc = -3; break; }
+        int lo = 0, hi = n - 1;
+        while (hi - lo > 1) { int mid = (lo + hi) / 2; if (u[mid] <= x) lo = mid; else hi = mid; }
+        double h = u[hi] - u[lo], t = (x - u[lo]) / h, s = 1.0 - t;
+        out[q] = s * v[lo] + t * v[hi] + h * h / 6.0 * ((s * s * s - s) * M[lo] + (t * t * t - t) * M[hi]);
+    }
+    free(M); free(cp); free(dp);
+    return rc;
+}
+
+/* Step a0: Chebyshev coefficients a_n, n < N, of P(k) on [kmin, kmax] (Eq.
+ * cheb_pk): natural cubic spline of (ln k_i, ln P_i), P at the N Chebyshev
+ * k-nodes, then the transform of orc_cheb_dct. */
+int orc_fit(int N, double kmin, double kmax, int kmap, int ntab, const double *ktab, const double *ptab, double *a)
+{
+    if (N < 1 || ntab < 3) return -1;
+    double *u = (double *)malloc(sizeof(double) * ntab), *v = (double *)malloc(sizeof(double) * ntab);
+    double *t = (double *)malloc(sizeof(double) * N), *kn = (double *)malloc(sizeof(double) * N);
+    double *uq = (double *)malloc(sizeof(double) * N), *pv = (double *)malloc(sizeof(double) * N);
+    int rc = (!u || !v || !t || !kn || !uq || !pv) ? -2 : 0;
+    for (int i = 0; !rc && i < ntab; i++) {
+        if (!(ktab[i] > 0.0) || !(ptab[i] > 0.0)) { rc = -1; break; }
+        u[i] = log(ktab[i]); v[i] = log(ptab[i]);
+    }
+    if (!rc) rc = orc_cheb_knodes(N, kmin, kmax, kmap, t, kn);
+    for (int j = 0; !rc && j < N; j++) {
+        if (!(kn[j] > 0.0)) { rc = -1; break; }
+        uq[j] = log(kn[j]);
+    }
+    if (!rc) rc = orc_spline_natural(ntab, u, v, N, uq, pv);
+    if (!rc) {
+        for (int j = 0; j < N; j++) pv[j] = exp(pv[j]);
+        rc = orc_cheb_dct(N, pv, a);
+    }
+    free(u); free(v); free(t); free(kn); free(uq); free(pv);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Prefactors N(l) of Eqs. gg, gs, ss: 2/pi, (2/pi) sqrt((l+2)!/(l-2)!),     */
+/* (2/pi) (l+2)!/(l-2)!, with (l+2)!/(l-2)! = (l+2)(l+1) l (l-1).            */
+/* ------------------------------------------------------------------------- */
+double orc_prefactor(int type, int l)
+{
+    double L = (double)l;
+    double r = (L + 2.0) * (L + 1.0) * L * (L - 1.0);
+    if (type == 0) return 2.0 / ORC_PI;
+    if (type == 1) return 2.0 / ORC_PI * sqrt(r);
+    return 2.0 / ORC_PI * r;
+}
+
+/* Number of spectra for ng clustering and ns lensing tracers:
+ * gg (i <= j), then gs (every i, j), then ss (i <= j). */
+int orc_npairs(int ng, int ns)
+{
+    return ng * (ng + 1) / 2 + ng * ns + ns * (ns + 1) / 2;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Steps 5 and 6: w and C.                                                   */
+/*   w^{AB}_l(a, r) = D(chi_a) D(R_r chi_a) sum_n a_n T~^{AB}_{n;l}(a, r)      */
+/*   C^{AB}_{ij}(l) = N_AB(l) sum_a sum_r wchi_a wR_r chi_a                    */
+/*                    K_i^A(chi_a) K_j^B(R_r chi_a) w^{AB}_l(a, r)            */
+/* Inputs: T[t][e][n][q] (q = a Rn + r), kernels kchi[tr][a] and              */
+/* kRchi[tr][q] (tracers 0..ng-1 clustering, ng..ng+ns-1 lensing, the lensing */
+/* ones already divided by chi^2), growth Dchi[a], DRchi[q].                 */
+/* Output C[p][e] in the pair order of orc_npairs.                          */
+/* ------------------------------------------------------------------------- */
+int orc_cl(int n_ell, const int *ell, int X, int Rn, const double *chi, const double *wchi,
+           const double *R, const double *wR, int N, const double *T, const double *a,
+           int ng, int ns, const double *kchi, const double *kRchi,
+           const double *Dchi, const double *DRchi, double *C)
+{
+    (void)R;
+    if (n_ell < 1 || X < 1 || Rn < 1 || N < 1 || ng < 0 || ns < 0 || ng + ns < 1) return -1;
+    const int Q = X * Rn;
+    double *w = (double *)malloc(sizeof(double) * Q);
+    if (!w) return -2;
+    int p0[3] = {0, ng * (ng + 1) / 2, ng * (ng + 1) / 2 + ng * ns};
+    for (int t = 0; t < 3; t++) {
+        for (int e = 0; e < n_ell; e++) {
+            const double *Te = T + ((size_t)t * n_ell + e) * N * (size_t)Q;
+            for (int q = 0; q < Q; q++) {
+                double s = 0.0;
+                for (int n = 0; n < N; n++) s += a[n] * Te[(size_t)n * Q + q];
+                w[q] = Dchi[q / Rn] * DRchi[q] * s;
+            }
+            double pref = orc_prefactor(t, ell[e]);
+            int p = p0[t];
+            int nA = (t == 2) ? ns : ng, nB = (t == 0) ? ng : ns;
+            int offA = (t == 2) ? ng : 0, offB = (t == 0) ? 0 : ng;
+            for (int i = 0; i < nA; i++) {
+                for (int j = (t == 1 ? 0 : i); j < nB; j++) {
+                    const double *Ki = kchi + (size_t)(offA + i) * X;
+                    const double *Kj = kRchi + (size_t)(offB + j) * Q;
+                    double s = 0.0;
+                    for (int aa = 0; aa < X; aa++) {
+                        double sr = 0.0;
+                        for (int r = 0; r < Rn; r++) {
+                            int q = aa * Rn + r;
+                            sr += wR[r] * Kj[q] * w[q];
+                        }
+                        s += wchi[aa] * chi[aa] * Ki[aa] * sr;
+                    }
+                    C[(size_t)p * n_ell + e] = pref * s;
+                    p++;
+                }
+            }
+        }
+    }
+    free(w);
+    return 0;
+}
