@@ -1,0 +1,190 @@
+/*
+ * blast.h — C ABI of the GB300 beyond-Limber angular power spectrum library.
+ *
+ * The library computes, for every pair of tomographic tracers, the angular
+ * power spectrum of Eq. cls-general of Chiarenza et al. (arXiv:2410.03632),
+ *
+ *   C^{AB}_ij(l) = N_AB(l) int dchi1 W^A_i(chi1) int dchi2 W^B_j(chi2)
+ *                  int dk k^2 P(k, chi1, chi2) j_l(k chi1) j_l(k chi2) / ((k chi1)^a (k chi2)^b),
+ *
+ * without the Limber approximation, by the paper's method (Sec. 3):
+ *   (pre) basis integrals T~^{AB}_{n;l}(chi1, chi2) of Eq. t_tilde, once per grid;
+ *   (a0)  Chebyshev coefficients of P (Eqs. chebpoints, a2, dft, cheb_pk);
+ *   (a)   projected matter density w_l = sum_n c_n T~_{n;l} (Eq. pmd);
+ *   (b)   the chi-R quadrature of Eq. final_cls in its unsymmetrised form
+ *         (Eq. app1 with chi2 = R chi1) and the probe prefactor N_AB(l) of
+ *         Eqs. gg, ss, gs.
+ * The power spectrum is growth separable, P(k, chi1, chi2) = D(chi1) D(chi2) P(k)
+ * (Sec. 4.2.1), so c_n(chi1, chi2) = D(chi1) D(chi2) a_n.
+ *
+ * Units: chi in Mpc/h, k in h/Mpc.  Tracer types: g = clustering, s = lensing.
+ * Spectrum (pair) order in every output: gg (i <= j, row major), then gs
+ * (i clustering, j lensing, all pairs, row major), then ss (i <= j).
+ * Output arrays are row major C[pair][ell], ells in plan order restricted to
+ * the request's ell mask.
+ *
+ * Conventions for every entry point:
+ *   - the return value is a blast_status (0 = success, negative = error);
+ *   - on BLAST_EINVAL nothing is written to any output;
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *   - the library owns plans, basis tables, work space and servers; the caller
+ *     owns request arrays and output arrays;
+ *   - a plan may be used by one call at a time (its work space is reused);
+ *     concurrent evaluation goes through a server, which owns per-slot space;
+ *   - pointers tagged "host or device" follow the request's mem_space.
+ */
+#ifndef BLAST_H
+#define BLAST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct blast_plan blast_plan;
+typedef struct blast_server blast_server;
+
+typedef enum {
+    BLAST_OK = 0,
+    BLAST_EINVAL = -1,    /* bad argument; no output written */
+    BLAST_ENOMEM = -2,    /* device or host allocation failed, or over budget */
+    BLAST_ENOTREADY = -3, /* result not ready yet (poll) */
+    BLAST_ETIMEOUT = -4,  /* a bounded wait ran out */
+    BLAST_EDEVICE = -5,   /* a CUDA call failed */
+    BLAST_ENOBASIS = -6,  /* the requested precision's basis table is absent */
+    BLAST_EBUSY = -7      /* server queue full */
+} blast_status;
+
+/* Arithmetic of contraction (a) and quadrature (b).  The Chebyshev fit and the
+ * basis precompute are always FP64. */
+typedef enum {
+    BLAST_FP64 = 0,   /* FP64 on CUDA cores (reference GPU path) */
+    BLAST_FP32 = 1,   /* FP32 basis, FP32 CUDA-core contraction, FP64 final sums */
+    BLAST_BF16X3 = 2  /* batched tcgen05 contraction: BF16 hi+lo split operands,
+                         three MMAs (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+} blast_precision;
+
+/* Bits of the precisions_mask of blast_precompute_basis. */
+#define BLAST_BASIS_FP64 (1u << 0)
+#define BLAST_BASIS_FP32 (1u << 1)
+#define BLAST_BASIS_BF16X2 (1u << 2)
+
+/* Grid and size description of a plan (Sec. 3.2 of the paper).
+ *   ell      n_ell integer multipoles, 2 <= ell, strictly increasing, n_ell <= 128
+ *   chi      n_chi evenly spaced nodes on [chi_min, chi_max], composite Simpson
+ *            weights (3/8 rule on the last three intervals when n_chi is even)
+ *   R        n_R nodes, two panels [R_min, 1] and [1, R_max] of n_R/2 first-kind
+ *            Chebyshev points each with Fejer-1 weights (n_R even, R_min < 1 < R_max)
+ *   k        n_cheb Chebyshev coefficients over [k_min, k_max]; k_map 0 maps k
+ *            linearly onto [-1, 1], k_map 1 maps ln k linearly
+ *   n_kquad  Clenshaw-Curtis points of the basis k integral, 2^m + 1
+ *   max_clust, max_lens  largest tracer counts a request may carry
+ *   device   CUDA device ordinal that holds the plan's tables               */
+typedef struct {
+    int n_ell;
+    const int32_t *ell;
+    int n_chi;
+    double chi_min, chi_max;
+    int n_R;
+    double R_min, R_max;
+    int n_cheb;
+    double k_min, k_max;
+    int k_map;
+    int n_kquad;
+    int max_clust, max_lens;
+    int device;
+} blast_plan_desc;
+
+/* One cosmology.  Tracers 0..n_clust-1 are clustering, n_clust..n_clust+n_lens-1
+ * lensing; kernels are the paper's calligraphic K of Eq. final_cls (lensing
+ * kernels already divided by chi^2).  All arrays float64, row major, host or
+ * device per mem_space, and only read during the call.
+ *   kern_chi     [n_clust+n_lens][n_chi]          K at chi_a
+ *   kern_Rchi    [n_clust+n_lens][n_chi*n_R]      K at R_r chi_a, index a*n_R + r
+ *   growth_chi   [n_chi]                          D(chi_a)
+ *   growth_Rchi  [n_chi*n_R]                      D(R_r chi_a)
+ *   k_tab, p_tab [n_ptab] linear P(k): k strictly increasing, P > 0, 3 <= n_ptab <= 1024,
+ *                and [k_tab[0], k_tab[n_ptab-1]] must contain every Chebyshev k-node
+ *   ell_mask_lo/hi  bit e selects plan ell e (lo: e < 64, hi: 64 <= e < 128); 0,0 = all
+ *   mem_space    0 = host pointers, 1 = device pointers                      */
+typedef struct {
+    int n_clust, n_lens;
+    const double *kern_chi;
+    const double *kern_Rchi;
+    const double *growth_chi;
+    const double *growth_Rchi;
+    int n_ptab;
+    const double *k_tab;
+    const double *p_tab;
+    uint64_t ell_mask_lo, ell_mask_hi;
+    int mem_space;
+} blast_request;
+
+/* Build a plan: host grids (Simpson, Fejer-1, Clenshaw-Curtis weights, Chebyshev
+ * nodes) and device tables for desc->device.  The basis is NOT computed here.
+ * Errors: BLAST_EINVAL (bad description), BLAST_ENOMEM, BLAST_EDEVICE.      */
+int blast_plan_create(const blast_plan_desc *desc, blast_plan **out);
+
+/* Free a plan and every device buffer it owns.  NULL is accepted. */
+int blast_plan_destroy(blast_plan *plan);
+
+/* Copy the plan's nodes to host arrays (any of them may be NULL):
+ * chi[n_chi], R[n_R], k_cheb[n_cheb] (the k of each Chebyshev point t_j =
+ * cos((2j+1) pi / 2 n_cheb), Eq. chebpoints).  Callers sample their kernels
+ * and growth at chi_a and R_r chi_a. */
+int blast_plan_nodes(const blast_plan *plan, double *chi, double *R, double *k_cheb);
+
+/* Number of spectra for a tracer count, in the pair order above. */
+int blast_npairs(int n_clust, int n_lens);
+
+/* Step (pre), Eq. t_tilde: compute T~^{AB}_{n;l}(chi_a, R_r chi_a) for the
+ * three types gg (f = k^2), gs (f = 1), ss (f = 1/k^2) in FP64 on the device,
+ * then derive the copies named in precisions_mask (FP64 is always kept).
+ * Synchronous with respect to the host when it returns.  Errors: BLAST_EDEVICE. */
+int blast_precompute_basis(blast_plan *plan, unsigned precisions_mask, void *stream);
+
+/* Copy the FP64 basis between the plan and a caller buffer of
+ * 3*n_ell*n_cheb*n_chi*n_R doubles laid out [type][ell][n][a*n_R + r]
+ * (mem_space 0 host, 1 device).  basis_set replaces the basis and rebuilds the
+ * reduced-precision copies named in precisions_mask.  Errors: BLAST_ENOBASIS
+ * (get before any basis exists), BLAST_EDEVICE. */
+int blast_basis_get(const blast_plan *plan, double *dst, int mem_space, void *stream);
+int blast_basis_set(blast_plan *plan, const double *src, int mem_space,
+                    unsigned precisions_mask, void *stream);
+
+/* Save / load the FP64 basis to a file with a header (magic, grid sizes, grid
+ * checksum) and a payload checksum; load rejects a file made for another grid
+ * with BLAST_EINVAL and rebuilds the reduced-precision copies in precisions_mask. */
+int blast_basis_save(const blast_plan *plan, const char *path);
+int blast_basis_load(blast_plan *plan, const char *path, unsigned precisions_mask);
+
+/* Steps (a0), (a), (b) for one cosmology.  cl_out[npairs][n_sel] receives FP64
+ * C_l (n_sel = ells selected by the mask), host or device per out_mem_space.
+ * With a host output the call waits for the stream; otherwise it is stream
+ * ordered.  BLAST_BF16X3 is served by the FP32 CUDA-core path for a single
+ * request (a one-row GEMM does not use tensor cores).
+ * Errors: BLAST_EINVAL, BLAST_ENOBASIS, BLAST_EDEVICE. */
+int blast_cl(blast_plan *plan, const blast_request *req, int precision,
+             double *cl_out, int out_mem_space, void *stream);
+
+/* The same for n cosmologies in one pass: every request has its own P(k),
+ * kernels, growth, tracer counts (<= the plan maxima) and ell mask.  outs[i]
+ * receives request i's C (layout as blast_cl).  BLAST_BF16X3 runs contraction
+ * (a) as one tcgen05 GEMM over the batch (cosmologies x Chebyshev order x
+ * chi-R nodes) with quadrature (b) fused in its epilogue. */
+int blast_cl_batch(blast_plan *plan, int n, const blast_request *reqs, int precision,
+                   double *const *outs, int out_mem_space, void *stream);
+
+/* Device bytes one request occupies while in flight (inputs, coefficients,
+ * weights, partial sums, outputs); the server admits requests against it. */
+size_t blast_request_footprint(const blast_plan *plan, const blast_request *req);
+
+/* Human-readable name of a status code (static string). */
+const char *blast_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BLAST_H */

@@ -1,0 +1,290 @@
+// Step (pre): the cosmology-independent basis integrals of Eq. t_tilde,
+//   T~^{AB}_{n;l}(chi_a, R_r chi_a) = int_{kmin}^{kmax} dk f^{AB}(k) T_n(x(k)) j_l(k chi_a) j_l(k R_r chi_a),
+// f^gg = k^2, f^gs = 1, f^ss = 1/k^2, by the Clenshaw-Curtis rule of Sec. 3.2:
+// a GEMM over the k nodes m,
+//   T~[t n][l, q] = sum_m A[m][t n] B_l[m][q],  A = w_m f_t(k_m) T_n(x_m),
+//   B_l[m][q]    = j_l(k_m chi_a) j_l(k_m R_r chi_a),
+// with B generated on chip from spherical Bessel recurrences in FP64.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "blast_internal.h"
+
+namespace {
+
+constexpr int kG = 8;     // plan ells per CTA (one group)
+constexpr int kRT = 8;    // R nodes per CTA
+constexpr int kMC = 28;   // k nodes per chunk: (1 + kRT) * kMC = 252 Bessel chains per chunk
+constexpr int kThreads = 256;
+
+// A[m][t*N + n] = w_m f_t(k_m) T_n(x(k_m)); T_n by the three-term recurrence.
+__global__ void k_basis_A(const double *__restrict__ kq, const double *__restrict__ wq, int Nk, int N,
+                          int kmap, double kmin, double kmax, double *__restrict__ A)
+{
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= Nk) return;
+    double k = kq[m];
+    double x = (kmap == 0) ? (2.0 * k - kmin - kmax) / (kmax - kmin)
+                           : 2.0 * (log(k) - log(kmin)) / (log(kmax) - log(kmin)) - 1.0;
+    x = fmin(1.0, fmax(-1.0, x));
+    double f0 = wq[m] * k * k, f1 = wq[m], f2 = wq[m] / (k * k);
+    double *row = A + (size_t)m * 3 * N;
+    double tprev = 1.0, tcur = x;
+    for (int n = 0; n < N; n++) {
+        double Tn;
+        if (n == 0) Tn = 1.0;
+        else if (n == 1) Tn = x;
+        else { Tn = 2.0 * x * tcur - tprev; tprev = tcur; tcur = Tn; }
+        row[n] = f0 * Tn;
+        row[N + n] = f1 * Tn;
+        row[2 * N + n] = f2 * Tn;
+    }
+}
+
+// j_l(x) for the (at most kG) ascending multipoles lg[0..ng) of one group.
+// x > lhi: forward recurrence from j_0, j_1 (stable for l < x).
+// x <= lhi: Miller's backward recurrence from lhi + 20 + 10 lhi^(1/3), scaled
+// by the least-squares match of the recurrence's two lowest orders to the
+// closed forms of j_0 and j_1.  Values below 1e-323 (j_l(x) <= (e x / 2l)^l)
+// are returned as zero without a recurrence.
+__device__ void jl_group(double x, const int *lg, int ng, double *out)
+{
+#pragma unroll
+    for (int g = 0; g < kG; g++) out[g] = 0.0;
+    if (ng <= 0 || !(x > 0.0)) return;
+    const int llo = lg[0], lhi = lg[ng - 1];
+    if ((double)llo * log(2.718281828459045 * x / (2.0 * llo)) < -744.0) return;
+    double s, c;
+    sincos(x, &s, &c);
+    const double inv = 1.0 / x;
+    double j0 = s * inv;
+    double j1 = (x < 1e-2) ? x * (1.0 / 3.0 - x * x / 30.0 + x * x * x * x / 840.0) : (j0 - c) * inv;
+    if (x > (double)lhi) {
+        double jm = j0, jc = j1;
+        int gi = 0;
+        while (gi < ng && lg[gi] <= 1) { out[gi] = (lg[gi] == 0) ? j0 : j1; gi++; }
+        double dl = 3.0;  // 2l + 1 at l = 1, exact in double
+        for (int l = 1; l < lhi; l++) {
+            double jn = (dl * inv) * jc - jm;  // j_{l+1}
+            dl += 2.0;
+            jm = jc;
+            jc = jn;
+            if (gi < ng && l + 1 == lg[gi]) { out[gi] = jc; gi++; }
+        }
+        return;
+    }
+    const int l0 = lhi + 20 + (int)(10.0 * cbrt((double)lhi));
+    double fp = 0.0, f = 1e-200;
+    int gi = ng - 1;
+    double dl = 2.0 * l0 + 1.0;  // exact in double
+    for (int l = l0; l > 0; l--) {
+        if (gi >= 0 && l == lg[gi]) { out[gi] = f; gi--; }
+        double fm = (dl * inv) * f - fp;  // f_{l-1}
+        dl -= 2.0;
+        fp = f;
+        f = fm;
+        if ((l & 3) == 0 && fabs(f) > 1e200) {
+            f *= 1e-200;
+            fp *= 1e-200;
+#pragma unroll
+            for (int g = 0; g < kG; g++)
+                if (g > gi) out[g] *= 1e-200;
+        }
+    }
+    // f = f_0, fp = f_1 (arbitrary scale): normalise before squaring
+    const double mx = fmax(fabs(f), fabs(fp));
+    f /= mx;
+    fp /= mx;
+    double scale = (j0 * f + j1 * fp) / ((f * f + fp * fp) * mx);
+#pragma unroll
+    for (int g = 0; g < kG; g++) out[g] *= scale;
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kThreads)
+k_basis_gemm(const double *__restrict__ A, const double *__restrict__ kq, int Nk, int N,
+             const int *__restrict__ ell, int L, int e0, const double *__restrict__ chi,
+             const double *__restrict__ R, int Rn, int Q, double *__restrict__ T)
+{
+    extern __shared__ double sm[];
+    const int rows3 = 3 * N;
+    double *As = sm;                           // [kMC][3N]
+    double *Jv = As + kMC * rows3;             // [(1+kRT) kMC][kG]
+    double *Bp = Jv + (1 + kRT) * kMC * kG;    // [kMC][kG*kRT]
+    __shared__ int lg[kG];
+
+    const int tid = threadIdx.x;
+    const int a = blockIdx.y;
+    const int r0 = blockIdx.x * kRT;
+    const int ng = min(kG, L - e0);
+    if (tid < kG) lg[tid] = (tid < ng) ? ell[e0 + tid] : 0;
+    const double chia = chi[a];
+    const int rb = tid >> 3, cb = tid & 7;
+    double acc[ROWS][kG];
+#pragma unroll
+    for (int i = 0; i < ROWS; i++)
+#pragma unroll
+        for (int g = 0; g < kG; g++) acc[i][g] = 0.0;
+    __syncthreads();
+
+    for (int m0 = 0; m0 < Nk; m0 += kMC) {
+        const int mcnt = min(kMC, Nk - m0);
+        const double *Asrc = A + (size_t)m0 * rows3;
+        for (int i = tid; i < mcnt * rows3; i += kThreads) As[i] = Asrc[i];
+        if (tid < (1 + kRT) * kMC) {
+            const int mi = tid % kMC, side = tid / kMC;
+            double out[kG];
+            const int r = r0 + side - 1;
+            bool ok = mi < mcnt && (side == 0 || r < Rn);
+            double dist = (side == 0) ? chia : (ok ? R[r] * chia : 0.0);
+            if (ok) jl_group(kq[m0 + mi] * dist, lg, ng, out);
+            else {
+#pragma unroll
+                for (int g = 0; g < kG; g++) out[g] = 0.0;
+            }
+#pragma unroll
+            for (int g = 0; g < kG; g++) Jv[tid * kG + g] = out[g];
+        }
+        __syncthreads();
+        for (int i = tid; i < kMC * kG * kRT; i += kThreads) {
+            const int mi = i / (kG * kRT), cmb = i % (kG * kRT);
+            const int g = cmb / kRT, rr = cmb % kRT;
+            Bp[i] = Jv[mi * kG + g] * Jv[((1 + rr) * kMC + mi) * kG + g];
+        }
+        __syncthreads();
+        for (int mi = 0; mi < mcnt; mi++) {
+            double b[kG];
+#pragma unroll
+            for (int g = 0; g < kG; g++) b[g] = Bp[mi * kG * kRT + g * kRT + cb];
+#pragma unroll
+            for (int i = 0; i < ROWS; i++) {
+                const int row = rb + 32 * i;
+                const double av = (row < rows3) ? As[mi * rows3 + row] : 0.0;
+#pragma unroll
+                for (int g = 0; g < kG; g++) acc[i][g] = fma(av, b[g], acc[i][g]);
+            }
+        }
+        __syncthreads();
+    }
+    const int r = r0 + cb;
+    if (r >= Rn) return;
+#pragma unroll
+    for (int i = 0; i < ROWS; i++) {
+        const int row = rb + 32 * i;
+        if (row >= rows3) continue;
+        const int t = row / N, n = row % N;
+#pragma unroll
+        for (int g = 0; g < kG; g++) {
+            if (g >= ng) continue;
+            T[(((size_t)t * L + e0 + g) * N + n) * Q + (size_t)a * Rn + r] = acc[i][g];
+        }
+    }
+}
+
+// FP64 basis -> FP32 copy (same layout) and BF16 hi/lo copies transposed to
+// [t][l][q][Nk16] (Chebyshev index fastest, zero padded): the K-major operand
+// layout of the tensor-core contraction.
+__global__ void k_basis_to_f32(const double *__restrict__ T, float *__restrict__ T32, size_t n)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) T32[i] = (float)T[i];
+}
+
+__global__ void k_basis_to_bf16(const double *__restrict__ T, int N, int Q, int Nk16,
+                                uint16_t *__restrict__ hi, uint16_t *__restrict__ lo)
+{
+    extern __shared__ double tile[];  // [N][64]
+    const int tl = blockIdx.y;        // t*L + e
+    const int q0 = blockIdx.x * 64;
+    const double *src = T + (size_t)tl * N * Q;
+    for (int i = threadIdx.x; i < N * 64; i += blockDim.x) {
+        int n = i / 64, qq = i % 64;
+        tile[i] = (q0 + qq < Q) ? src[(size_t)n * Q + q0 + qq] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * Nk16; i += blockDim.x) {
+        int qq = i / Nk16, n = i % Nk16;
+        if (q0 + qq >= Q) continue;
+        double v = (n < N) ? tile[n * 64 + qq] : 0.0;
+        __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+        double rem = v - (double)__bfloat162float(h);
+        __nv_bfloat16 l = __float2bfloat16_rn((float)rem);
+        size_t o = ((size_t)tl * Q + q0 + qq) * Nk16 + n;
+        hi[o] = __bfloat16_as_ushort(h);
+        lo[o] = __bfloat16_as_ushort(l);
+    }
+}
+
+template <int ROWS>
+int launch_gemm_rows(blast_plan *p, const double *A, const double *kq, const int *ell, const double *R,
+                     cudaStream_t s)
+{
+    size_t smem = sizeof(double) * ((size_t)kMC * 3 * p->N + (size_t)(1 + kRT) * kMC * kG + (size_t)kMC * kG * kRT);
+    BL_CUDA(cudaFuncSetAttribute(k_basis_gemm<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((p->Rn + kRT - 1) / kRT, p->X);
+    for (int e0 = 0; e0 < p->L; e0 += kG) {
+        k_basis_gemm<ROWS><<<grid, kThreads, smem, s>>>(A, kq, p->Nk, p->N, ell, p->L, e0, p->d_chi, R,
+                                                        p->Rn, p->Q, p->T64);
+        BL_CUDA(cudaGetLastError());
+    }
+    return BLAST_OK;
+}
+
+}  // namespace
+
+int launch_basis(blast_plan *p, cudaStream_t s)
+{
+    const int rows3 = 3 * p->N;
+    if (rows3 > 32 * 12) return BLAST_EINVAL;  // n_cheb <= 128 (ROWS <= 12)
+    double *kq = nullptr, *wq = nullptr, *A = nullptr, *R = nullptr;
+    int *ell = nullptr;
+    int rc = BLAST_OK;
+    size_t nA = (size_t)p->Nk * rows3;
+    if (cudaMalloc(&kq, sizeof(double) * p->Nk) || cudaMalloc(&wq, sizeof(double) * p->Nk) ||
+        cudaMalloc(&A, sizeof(double) * nA) || cudaMalloc(&R, sizeof(double) * p->Rn) ||
+        cudaMalloc(&ell, sizeof(int) * p->L)) {
+        cudaGetLastError();
+        rc = BLAST_ENOMEM;
+    }
+    if (!rc && (cudaMemcpyAsync(kq, p->kq.data(), sizeof(double) * p->Nk, cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(wq, p->wq.data(), sizeof(double) * p->Nk, cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(R, p->R.data(), sizeof(double) * p->Rn, cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(ell, p->ell.data(), sizeof(int) * p->L, cudaMemcpyHostToDevice, s)))
+        rc = BLAST_EDEVICE;
+    if (!rc) {
+        k_basis_A<<<(p->Nk + 255) / 256, 256, 0, s>>>(kq, wq, p->Nk, p->N, p->kmap, p->k_min, p->k_max, A);
+        if (cudaGetLastError() != cudaSuccess) rc = BLAST_EDEVICE;
+    }
+    if (!rc) {
+        int rows = (rows3 + 31) / 32;
+        if (rows <= 3) rc = launch_gemm_rows<3>(p, A, kq, ell, R, s);
+        else if (rows <= 6) rc = launch_gemm_rows<6>(p, A, kq, ell, R, s);
+        else if (rows <= 9) rc = launch_gemm_rows<9>(p, A, kq, ell, R, s);
+        else rc = launch_gemm_rows<12>(p, A, kq, ell, R, s);
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(kq); cudaFree(wq); cudaFree(A); cudaFree(R); cudaFree(ell);
+    if (!rc && cudaGetLastError() != cudaSuccess) rc = BLAST_EDEVICE;
+    return rc;
+}
+
+int launch_basis_convert(blast_plan *p, unsigned mask, cudaStream_t s)
+{
+    size_t n = (size_t)3 * p->L * p->N * p->Q;
+    if ((mask & BLAST_BASIS_FP32) && p->T32) {
+        k_basis_to_f32<<<152 * 8, 256, 0, s>>>(p->T64, p->T32, n);
+        BL_CUDA(cudaGetLastError());
+        p->have32 = true;
+    }
+    if ((mask & BLAST_BASIS_BF16X2) && p->Tbf_hi) {
+        size_t smem = sizeof(double) * p->N * 64;
+        BL_CUDA(cudaFuncSetAttribute(k_basis_to_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dim3 grid((p->Q + 63) / 64, 3 * p->L);
+        k_basis_to_bf16<<<grid, 256, smem, s>>>(p->T64, p->N, p->Q, p->Nk16, p->Tbf_hi, p->Tbf_lo);
+        BL_CUDA(cudaGetLastError());
+        p->havebf = true;
+    }
+    return BLAST_OK;
+}
