@@ -1,0 +1,374 @@
+"""Benchmark: beyond-Limber C_l sets per second on one or more GB300s.
+
+Workload: the 3x2pt data vector with 5 clustering + 5 lensing tomographic bins
+(55 spectra), 64 log-spaced ells in 2..1000, n_chi = 128, n_R = 128 in
+R in [0.2, 1.8], Chebyshev order 64, for a batch of seeded synthetic
+cosmologies (each with its own P(k), kernels and growth).  One step is one
+pass of the whole hot path — Chebyshev fit, weights, contraction (a) and
+quadrature (b) — over the batch.  The basis precompute is excluded, as in the
+paper's timings.
+
+The headline value is the mixed-precision batched path (tcgen05 BF16 five-slice
+exact split when the plan supports it); the plain FP64 GPU path is measured
+beside it with the headline's error against the FP64 result stated.  Usage:
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl blast|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "C_l-sets/sec (3x2pt, all bin pairs) mixed vs FP64 at ≤1e-4 rel err; p50/p99 latency"
+UNIT = "C_l-sets/s"
+WORKLOAD = ("3x2pt, 5 clustering + 5 lensing bins (55 spectra), 64 log-spaced ells 2..1000, "
+            "n_chi=128, n_R=128 (R in [0.2,1.8]), Chebyshev order 64, n_kquad=65537")
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu, self.proc, self.path = gpu, None, None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- oracle (CPU) timing
+def oracle_sample(n_req=4, ell_stride=4, seed=7):
+    """Time the FP64 oracle's per-cosmology evaluation (fit + contraction +
+    quadrature; the basis is excluded as in the paper) on the benchmark grid
+    for a subset of ells.  The oracle's basis for this grid would take hours
+    to build on the host, and its evaluation loops cost the same whatever the
+    basis values are, so the sample feeds it a seeded random basis of the
+    right shape.  Returns (C_l-sets/s, seconds, description, threads)."""
+    import oracle
+    from paper_2410_03632_gb300 import synth
+    spec = synth.plan_spec("c1")
+    g = oracle.Grid(spec.ells, spec.n_chi, spec.chi_min, spec.chi_max, spec.n_R, spec.R_min, spec.R_max,
+                    spec.n_cheb, spec.k_min, spec.k_max, spec.n_kquad, spec.k_map)
+    sub = spec.ells[::ell_stride]
+    rng = np.random.default_rng(seed)
+    T = rng.standard_normal((3, sub.size, spec.n_cheb, spec.n_chi * spec.n_R))
+    rqs = [synth.config_request("c1", g.chi, g.R, 1 + i) for i in range(n_req)]
+    t0 = time.perf_counter()
+    for rq in rqs:
+        a = g.fit(rq.k_tab, rq.p_tab)
+        g.cl(T, a, rq.n_clust, rq.n_lens, rq.kern_chi, rq.kern_Rchi, rq.growth_chi, rq.growth_Rchi,
+             ell_subset=sub)
+    dt = time.perf_counter() - t0
+    sets = n_req * sub.size / spec.ells.size
+    desc = (f"{n_req} cosmologies x {sub.size} of 64 ells (every {ell_stride}th) on the benchmark grid, "
+            f"oracle fit + contraction + quadrature, seeded random basis of the right shape; "
+            f"scaled to full C_l-sets")
+    return sets / dt, dt, desc, 1
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(n_req=1)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        v, dt, desc, cores = oracle_sample(n_req=1)
+        vals.append(v)
+        secs += dt
+    value = args.steps * (1 * 16 / 64) / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+def traffic_for(kernel_file, kernel_name):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json for the
+    current source of the kernel (None when the source changed since)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_2410_03632_gb300", "csrc", kernel_file), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    for rec in json.load(open(path)):
+        if rec.get("kernel") == kernel_name and rec.get("src_sha") == sha:
+            return rec.get("bytes_per_launch_full")
+    return None
+
+
+def run_blast(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2410_03632_gb300 import blast as bl
+    from paper_2410_03632_gb300 import synth
+    from tests.metrics import eij
+
+    rank, local, world = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    spec = synth.plan_spec("c1")
+    plan = bl.Plan(spec, device=local)
+    cache = args.basis_cache
+    if cache and os.path.exists(cache):
+        bl.blast_basis_load(plan.h, cache, bl.BASIS_ALL)
+    else:
+        plan.precompute(bl.BASIS_ALL)
+        if cache and rank == 0:
+            bl.blast_basis_save(plan.h, cache)
+    chi, R, _ = plan.nodes()
+    B = args.batch
+    rqs = [synth.config_request("c1", chi, R, 1 + i + rank * B) for i in range(B)]
+    fields = ["kern_chi", "kern_Rchi", "growth_chi", "growth_Rchi", "k_tab", "p_tab"]
+    dev_arrays = [{f: torch.from_numpy(np.ascontiguousarray(getattr(rq, f))).to(dev) for f in fields} for rq in rqs]
+    reqs = [plan.request(rq, device_arrays=d) for rq, d in zip(rqs, dev_arrays)]
+    P = bl.blast_npairs(5, 5)
+    outs = [torch.empty((P, plan.L), dtype=torch.float64, device=dev) for _ in range(B)]
+    out_ptrs = [o.data_ptr() for o in outs]
+    stream = torch.cuda.current_stream(dev)
+
+    have_tc = bl.blast_cl_batch(plan.h, reqs[:2], bl.BLAST_BF16S, out_ptrs[:2], 1, stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    prec_main = bl.BLAST_BF16S if have_tc else bl.BLAST_FP32
+    dtype_main = "bf16 5-slice exact split (tcgen05)" if have_tc else "f32"
+
+    def step(prec):
+        rc = bl.blast_cl_batch(plan.h, reqs, prec, out_ptrs, 1, stream.cuda_stream)
+        if rc != 0:
+            raise RuntimeError(f"blast_cl_batch failed: {bl.blast_status_str(rc)}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(prec, K, W, profile=False):
+        for _ in range(W):
+            step(prec)
+        torch.cuda.synchronize()
+        barrier()
+        bl.blast_profile_reset(plan.h)
+        bl.blast_profile_enable(plan.h, profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            step(prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        prof = {}
+        for c, name in enumerate(bl.KERNEL_CLASS_NAMES):
+            prof[name] = bl.blast_profile_read(plan.h, c)
+        bl.blast_profile_enable(plan.h, False)
+        return ms, prof
+
+    clk = ClockSampler(local)
+    clk.start()
+    ms_main, prof_main = timed(prec_main, args.steps, args.warmup, profile=True)
+    clocks = clk.stop()
+    C_main = [o.cpu().numpy() for o in outs]
+    k64 = max(2, args.steps // 4)
+    ms_64, _ = timed(bl.BLAST_FP64, k64, 1)
+    C_64 = [o.cpu().numpy() for o in outs]
+    err = max(float(np.max(eij(a, b, 5, 5))) for a, b in zip(C_main, C_64))
+
+    # contraction kernel roofline (dominant kernel of the step)
+    kname = "contract_tc" if have_tc else "contract"
+    kms, klaunch = prof_main[kname]
+    avg_ms = kms / max(1, klaunch)
+    L, N, Q, X = plan.L, plan.N, plan.Q, plan.X
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    if have_tc:
+        # 15 BF16 slice products per coefficient-basis product, K padded to 64
+        flops = 2.0 * 3 * L * 64 * Q * (-(-B // 128) * 128) * 15
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_kind": "bf16 sustained, of measured",
+                "traffic": traffic_for("contract_tc.cu", "contract_tc")}
+    else:
+        ntr = 10
+        alg_bytes = 3 * L * N * Q * 4 + B * (ntr * Q * 4 + N * 4 + 3 * L * X * 5 * 4)
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": "hbm copy, of measured", "traffic": traffic_for("eval.cu", "k_contract<float>")}
+    roof["kernel"] = kname
+    roof["avg_launch_ms"] = avg_ms
+    roof["launches"] = klaunch
+
+    # single-request latency (p50 / p99) of the mixed path
+    lat = []
+    one_prec = bl.BLAST_FP32
+    for i in range(3):
+        bl.blast_cl(plan.h, reqs[0], one_prec, out_ptrs[0], 1, stream.cuda_stream)
+    torch.cuda.synchronize()
+    for i in range(50):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bl.blast_cl(plan.h, reqs[i % B], one_prec, out_ptrs[i % B], 1, stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+    lat.sort()
+
+    # end to end through the C ABI with host buffers (pinned)
+    host = []
+    h2d = 0
+    for rq in rqs:
+        d = {}
+        for f in fields:
+            arr = np.ascontiguousarray(getattr(rq, f))
+            t = torch.empty(arr.shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = arr
+            d[f] = t
+            h2d += arr.nbytes
+        host.append(d)
+    hreqs = [plan.request(rq, device_arrays=None) for rq in rqs]
+    for hr, d in zip(hreqs, host):  # point the host request at pinned copies
+        hr.kern_chi, hr.kern_Rchi = d["kern_chi"].data_ptr(), d["kern_Rchi"].data_ptr()
+        hr.growth_chi, hr.growth_Rchi = d["growth_chi"].data_ptr(), d["growth_Rchi"].data_ptr()
+        hr.k_tab, hr.p_tab = d["k_tab"].data_ptr(), d["p_tab"].data_ptr()
+        hr._keep = d
+    houts = [torch.empty((P, plan.L), dtype=torch.float64, pin_memory=True) for _ in range(B)]
+    hptrs = [o.data_ptr() for o in houts]
+    d2h = sum(o.numel() * 8 for o in houts)
+
+    def e2e_step():
+        rc = bl.blast_cl_batch(plan.h, hreqs, prec_main, hptrs, 0, stream.cuda_stream)
+        if rc != 0:
+            raise RuntimeError(bl.blast_status_str(rc))
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    launches = sum(prof_main[n][1] for n in bl.KERNEL_CLASS_NAMES)
+    value = world * B * args.steps / (ms_main * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_main / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_main, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_per_gpu": B, "precision": dtype_main,
+                   "l2": "inputs larger than L2 (basis tables 0.8-1.6 GB per step)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "fp64": {"value": world * B * k64 / (ms_64 * 1e-3), "unit": UNIT, "ms_per_step": ms_64 / k64,
+                 "dtype": "f64"},
+        "err_vs_fp64": {"max_eij": err, "bound": 1e-4,
+                        "def": "|C-C_fp64|/sqrt(C_ii C_jj), every cosmology of the batch, all pairs and ells"},
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                       "what": "one cosmology, FP32 path, device inputs"},
+        "roofline": roof,
+        "e2e": {"value": world * B * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, desc, cores = oracle_sample()
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                                "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--impl", default="blast", choices=["blast", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--basis-cache", default=None,
+                    help="file to load the FP64 basis from (or save it to after computing it)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_blast(args)
+
+
+if __name__ == "__main__":
+    main()

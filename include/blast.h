@@ -62,14 +62,19 @@ typedef enum {
 typedef enum {
     BLAST_FP64 = 0,   /* FP64 on CUDA cores (reference GPU path) */
     BLAST_FP32 = 1,   /* FP32 basis, FP32 CUDA-core contraction, FP64 final sums */
-    BLAST_BF16X3 = 2  /* batched tcgen05 contraction: BF16 hi+lo split operands,
-                         three MMAs (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+    BLAST_BF16S = 2   /* batched tcgen05 contraction on BF16 tensor cores: the
+                         coefficients and the basis are each cut into five 8-bit
+                         fixed-point slices held exactly in BF16; the 15 slice
+                         products of total order <= 4 accumulate exactly in FP32
+                         TMEM and are combined exactly in 64-bit integers, so the
+                         Chebyshev sum keeps about 40 bits through the strong
+                         cancellation of Eq. pmd where P(k) is small */
 } blast_precision;
 
 /* Bits of the precisions_mask of blast_precompute_basis. */
 #define BLAST_BASIS_FP64 (1u << 0)
 #define BLAST_BASIS_FP32 (1u << 1)
-#define BLAST_BASIS_BF16X2 (1u << 2)
+#define BLAST_BASIS_BF16S (1u << 2)  /* slice tables of the tensor-core path */
 
 /* Grid and size description of a plan (Sec. 3.2 of the paper).
  *   ell      n_ell integer multipoles, 2 <= ell, strictly increasing, n_ell <= 128
@@ -163,23 +168,42 @@ int blast_basis_load(blast_plan *plan, const char *path, unsigned precisions_mas
 /* Steps (a0), (a), (b) for one cosmology.  cl_out[npairs][n_sel] receives FP64
  * C_l (n_sel = ells selected by the mask), host or device per out_mem_space.
  * With a host output the call waits for the stream; otherwise it is stream
- * ordered.  BLAST_BF16X3 is served by the FP32 CUDA-core path for a single
- * request (a one-row GEMM does not use tensor cores).
- * Errors: BLAST_EINVAL, BLAST_ENOBASIS, BLAST_EDEVICE. */
+ * ordered.  BLAST_BF16S runs the same tensor-core kernel as a batch of one.
+ * Errors: BLAST_EINVAL, BLAST_ENOBASIS, BLAST_EDEVICE, BLAST_ETIMEOUT (a bounded
+ * device wait of an earlier or this call gave up; the call's outputs are void). */
 int blast_cl(blast_plan *plan, const blast_request *req, int precision,
              double *cl_out, int out_mem_space, void *stream);
 
 /* The same for n cosmologies in one pass: every request has its own P(k),
  * kernels, growth, tracer counts (<= the plan maxima) and ell mask.  outs[i]
- * receives request i's C (layout as blast_cl).  BLAST_BF16X3 runs contraction
+ * receives request i's C (layout as blast_cl).  BLAST_BF16S runs contraction
  * (a) as one tcgen05 GEMM over the batch (cosmologies x Chebyshev order x
- * chi-R nodes) with quadrature (b) fused in its epilogue. */
+ * chi-R nodes) with the R sum of quadrature (b) fused in its epilogue; it
+ * needs n_R a multiple of 32, n_cheb <= 64 and at most 5 tracers of each kind
+ * (BLAST_EINVAL otherwise). */
 int blast_cl_batch(blast_plan *plan, int n, const blast_request *reqs, int precision,
                    double *const *outs, int out_mem_space, void *stream);
 
 /* Device bytes one request occupies while in flight (inputs, coefficients,
  * weights, partial sums, outputs); the server admits requests against it. */
 size_t blast_request_footprint(const blast_plan *plan, const blast_request *req);
+
+/* Kernel classes of the evaluation path, for blast_profile_read. */
+#define BLAST_K_FIT 0         /* step (a0): Chebyshev fit */
+#define BLAST_K_WEIGHTS 1     /* quadrature weights U, V with growth folded in */
+#define BLAST_K_CONTRACT 2    /* steps (a) + (b, sum over R) on CUDA cores */
+#define BLAST_K_CONTRACT_TC 3 /* steps (a) + (b, sum over R) on tcgen05 tensor cores */
+#define BLAST_K_REDUCE 4      /* step (b, sum over chi) and prefactor */
+#define BLAST_K_CLASSES 5
+
+/* Per-kernel device time.  While enabled, every evaluation call brackets each
+ * of its kernel launches with CUDA events recorded on the call's stream.
+ * blast_profile_read waits for those events and returns, for one kernel class,
+ * the summed device milliseconds and the launch count since the last reset
+ * (launches are counted whether or not timing is enabled). */
+int blast_profile_enable(blast_plan *plan, int enable);
+int blast_profile_read(blast_plan *plan, int kernel_class, double *total_ms, long long *launches);
+int blast_profile_reset(blast_plan *plan);
 
 /* Human-readable name of a status code (static string). */
 const char *blast_status_str(int status);

@@ -21,9 +21,9 @@ from . import build as _build
 
 BLAST_OK, BLAST_EINVAL, BLAST_ENOMEM, BLAST_ENOTREADY = 0, -1, -2, -3
 BLAST_ETIMEOUT, BLAST_EDEVICE, BLAST_ENOBASIS, BLAST_EBUSY = -4, -5, -6, -7
-BLAST_FP64, BLAST_FP32, BLAST_BF16X3 = 0, 1, 2
-BLAST_BASIS_FP64, BLAST_BASIS_FP32, BLAST_BASIS_BF16X2 = 1, 2, 4
-BASIS_ALL = BLAST_BASIS_FP64 | BLAST_BASIS_FP32 | BLAST_BASIS_BF16X2
+BLAST_FP64, BLAST_FP32, BLAST_BF16S = 0, 1, 2
+BLAST_BASIS_FP64, BLAST_BASIS_FP32, BLAST_BASIS_BF16S = 1, 2, 4
+BASIS_ALL = BLAST_BASIS_FP64 | BLAST_BASIS_FP32 | BLAST_BASIS_BF16S
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _vp = ctypes.c_void_p
@@ -82,6 +82,9 @@ def lib():
             L.blast_request_footprint.restype = sz
             L.blast_status_str.argtypes = [i]
             L.blast_status_str.restype = ctypes.c_char_p
+            L.blast_profile_enable.argtypes = [P, i]
+            L.blast_profile_read.argtypes = [P, i, _dp, ctypes.POINTER(ctypes.c_longlong)]
+            L.blast_profile_reset.argtypes = [P]
             _LIB = L
     return _LIB
 
@@ -135,6 +138,25 @@ def blast_request_footprint(h, req):
 
 def blast_status_str(rc):
     return lib().blast_status_str(rc).decode()
+
+
+BLAST_K_FIT, BLAST_K_WEIGHTS, BLAST_K_CONTRACT, BLAST_K_CONTRACT_TC, BLAST_K_REDUCE = 0, 1, 2, 3, 4
+KERNEL_CLASS_NAMES = ["fit", "weights", "contract", "contract_tc", "reduce"]
+
+
+def blast_profile_enable(h, enable):
+    _check(lib().blast_profile_enable(h, int(enable)), "blast_profile_enable")
+
+
+def blast_profile_read(h, cls):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(lib().blast_profile_read(h, cls, ctypes.byref(ms), ctypes.byref(n)), "blast_profile_read")
+    return ms.value, n.value
+
+
+def blast_profile_reset(h):
+    _check(lib().blast_profile_reset(h), "blast_profile_reset")
 
 
 # ---------------------------------------------------------------------------- helpers

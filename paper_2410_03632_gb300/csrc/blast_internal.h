@@ -11,6 +11,7 @@
 
 #define BLAST_MAX_ELL 128
 #define BLAST_MAX_TRACERS 32
+#define BLAST_TC_SLICES 5   // 8-bit fixed-point slices per operand on the tensor-core path
 
 // Status helpers -------------------------------------------------------------
 #define BL_CUDA(expr)                                                             \
@@ -41,6 +42,7 @@ struct Workspace {
     DevBuf ypart;   // partial sums Y[b][t][e][a][j]
     DevBuf cl;      // device C before scatter to the caller
     DevBuf meta;    // per-request descriptors
+    DevBuf tc;      // coefficient slices and scales of the tensor-core path
     std::vector<char> hmeta;
 };
 
@@ -65,13 +67,40 @@ struct blast_plan {
     // basis tables
     double *T64 = nullptr;          // [3][L][N][Q]
     float *T32 = nullptr;           // [3][L][N][Q]
-    uint16_t *Tbf_hi = nullptr;     // [3][L][Q][Nk16] bf16 high part, K-major (n fastest)
-    uint16_t *Tbf_lo = nullptr;     // [3][L][Q][Nk16] bf16 low part (T - hi, rounded)
-    int Nk16 = 0;                   // N rounded up to a multiple of 16 (zero padded)
+    uint16_t *Tsl = nullptr;        // [S][3 L Q][Kp] bf16 integer slices, K-major (n fastest)
+    float *scT = nullptr;           // [3 L Q] 2^(eT - 16 - 8(S-1)) per column
+    int Kp = 0;                     // N rounded up to a multiple of 64 (zero padded)
     bool have64 = false, have32 = false, havebf = false;
+    int *d_err = nullptr;           // host-mapped error word written by bounded device waits
+    int *h_err = nullptr;
 
     Workspace ws;
+
+    // per-kernel-class launch counts and (optional) event timing
+    bool prof_on = false;
+    long long launches[BLAST_K_CLASSES] = {0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[BLAST_K_CLASSES];
+    double prof_ms[BLAST_K_CLASSES] = {0};
 };
+
+// Run one launcher under the plan's profiler: count it, and when timing is on
+// bracket it with events on stream s.
+template <class F> int prof_launch(blast_plan *p, int cls, cudaStream_t s, F &&fn)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (p->prof_on) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    int rc = fn();
+    p->launches[cls]++;
+    if (p->prof_on) {
+        cudaEventRecord(b, s);
+        p->prof_ev[cls].emplace_back(a, b);
+    }
+    return rc;
+}
 
 // Request descriptor on the device (one per cosmology of a call).
 struct ReqDev {
@@ -96,7 +125,11 @@ int launch_contract(blast_plan *p, ReqDev *dreq, int nreq, int prec, const int *
 int launch_reduce(blast_plan *p, ReqDev *dreq, int nreq, int prec, const int *d_esel, int n_esel,
                   const void *ypart, cudaStream_t s);
 int launch_contract_tc(blast_plan *p, ReqDev *dreq, int nreq, const int *d_esel, int n_esel,
-                       void *ypart, void *coef_bf, cudaStream_t s);
+                       void *ypart, cudaStream_t s);
+int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int nreq, const int *d_esel, int n_esel,
+                     const void *ypart, cudaStream_t s);
+int launch_basis_slices(blast_plan *p, cudaStream_t s);
+bool tc_supported(const blast_plan *p);
 
 // Host helpers
 int plan_alloc_basis(blast_plan *p, unsigned mask);

@@ -422,8 +422,8 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
     int *de = reinterpret_cast<int *>(dreq + n);
     BL_CUDA(cudaMemcpyAsync(dreq, hreq.data(), sizeof(ReqDev) * n, cudaMemcpyHostToDevice, s));
     BL_CUDA(cudaMemcpyAsync(de, esel.data(), sizeof(int) * esel.size(), cudaMemcpyHostToDevice, s));
-    if ((rc = launch_fit(p, dreq, n, s))) return rc;
-    if ((rc = launch_weights(p, dreq, n, prec != BLAST_FP64, s))) return rc;
+    if ((rc = prof_launch(p, BLAST_K_FIT, s, [&] { return launch_fit(p, dreq, n, s); }))) return rc;
+    if ((rc = prof_launch(p, BLAST_K_WEIGHTS, s, [&] { return launch_weights(p, dreq, n, prec != BLAST_FP64, s); }))) return rc;
     *dreq_out = dreq;
     *d_esel = de;
     return BLAST_OK;
@@ -445,17 +445,22 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
                               int out_mem_space, void *stream)
 {
     if (!p || n < 1 || !reqs || !outs) return BLAST_EINVAL;
-    if (prec < BLAST_FP64 || prec > BLAST_BF16X3) return BLAST_EINVAL;
+    if (prec < BLAST_FP64 || prec > BLAST_BF16S) return BLAST_EINVAL;
     if (out_mem_space != 0 && out_mem_space != 1) return BLAST_EINVAL;
     for (int i = 0; i < n; i++) {
         int rc = validate_request(p, &reqs[i]);
         if (rc) return rc;
         if (!outs[i]) return BLAST_EINVAL;
     }
-    bool use_tc = (prec == BLAST_BF16X3 && n >= 2);
+    const bool use_tc = (prec == BLAST_BF16S);
+    if (use_tc && !tc_supported(p)) return BLAST_EINVAL;
     if (prec == BLAST_FP64 && !p->have64) return BLAST_ENOBASIS;
-    if (prec != BLAST_FP64 && !use_tc && !p->have32) return BLAST_ENOBASIS;
+    if (prec == BLAST_FP32 && !p->have32) return BLAST_ENOBASIS;
     if (use_tc && !p->havebf) return BLAST_ENOBASIS;
+    if (*p->h_err) {  // a bounded device wait of an earlier call gave up
+        *p->h_err = 0;
+        return BLAST_ETIMEOUT;
+    }
     BL_CUDA(cudaSetDevice(p->device));
     cudaStream_t s = (cudaStream_t)stream;
     ReqDev *dreq = nullptr;
@@ -463,17 +468,35 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
     std::vector<ReqDev> hreq;
     int rc = stage_batch(p, n, reqs, prec, outs, out_mem_space, s, &dreq, &d_esel, &n_esel, hreq);
     if (rc) return rc;
-    const size_t ybytes = (size_t)n * 3 * n_esel * p->X * p->max_tr * (prec == BLAST_FP64 ? 8 : 4);
-    if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
     if (use_tc) {
-        if ((rc = launch_contract_tc(p, dreq, n, d_esel, n_esel, p->ws.ypart.p, nullptr, s))) return rc;
-        if ((rc = launch_reduce(p, dreq, n, BLAST_FP32, d_esel, n_esel, p->ws.ypart.p, s))) return rc;
+        const size_t ybytes = (size_t)n * 3 * n_esel * p->X * (p->Rn / 32) * p->max_tr * 4;
+        if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
+        if ((rc = prof_launch(p, BLAST_K_CONTRACT_TC, s, [&] {
+                 return launch_contract_tc(p, dreq, n, d_esel, n_esel, p->ws.ypart.p, s);
+             })))
+            return rc;
+        if ((rc = prof_launch(p, BLAST_K_REDUCE, s, [&] {
+                 return launch_reduce_tc(p, dreq, n, d_esel, n_esel, p->ws.ypart.p, s);
+             })))
+            return rc;
     } else {
-        int cp = (prec == BLAST_FP64) ? BLAST_FP64 : BLAST_FP32;
-        if ((rc = launch_contract(p, dreq, n, cp, d_esel, n_esel, p->ws.ypart.p, s))) return rc;
-        if ((rc = launch_reduce(p, dreq, n, cp, d_esel, n_esel, p->ws.ypart.p, s))) return rc;
+        const size_t ybytes = (size_t)n * 3 * n_esel * p->X * p->max_tr * (prec == BLAST_FP64 ? 8 : 4);
+        if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
+        if ((rc = prof_launch(p, BLAST_K_CONTRACT, s, [&] {
+                 return launch_contract(p, dreq, n, prec, d_esel, n_esel, p->ws.ypart.p, s);
+             })))
+            return rc;
+        if ((rc = prof_launch(p, BLAST_K_REDUCE, s, [&] {
+                 return launch_reduce(p, dreq, n, prec, d_esel, n_esel, p->ws.ypart.p, s);
+             })))
+            return rc;
     }
-    return finish_batch(p, n, hreq, outs, out_mem_space, s);
+    rc = finish_batch(p, n, hreq, outs, out_mem_space, s);
+    if (!rc && out_mem_space == 0 && *p->h_err) {
+        *p->h_err = 0;
+        return BLAST_ETIMEOUT;
+    }
+    return rc;
 }
 
 extern "C" int blast_cl(blast_plan *p, const blast_request *req, int prec, double *cl_out, int out_mem_space,
@@ -482,4 +505,45 @@ extern "C" int blast_cl(blast_plan *p, const blast_request *req, int prec, doubl
     if (!req || !cl_out) return BLAST_EINVAL;
     double *outs[1] = {cl_out};
     return blast_cl_batch(p, 1, req, prec, outs, out_mem_space, stream);
+}
+
+extern "C" int blast_profile_enable(blast_plan *p, int enable)
+{
+    if (!p) return BLAST_EINVAL;
+    p->prof_on = enable != 0;
+    return BLAST_OK;
+}
+
+extern "C" int blast_profile_read(blast_plan *p, int cls, double *total_ms, long long *launches)
+{
+    if (!p || cls < 0 || cls >= BLAST_K_CLASSES) return BLAST_EINVAL;
+    BL_CUDA(cudaSetDevice(p->device));
+    for (auto &ev : p->prof_ev[cls]) {
+        float ms = 0.f;
+        BL_CUDA(cudaEventSynchronize(ev.second));
+        BL_CUDA(cudaEventElapsedTime(&ms, ev.first, ev.second));
+        p->prof_ms[cls] += ms;
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    p->prof_ev[cls].clear();
+    if (total_ms) *total_ms = p->prof_ms[cls];
+    if (launches) *launches = p->launches[cls];
+    return BLAST_OK;
+}
+
+extern "C" int blast_profile_reset(blast_plan *p)
+{
+    if (!p) return BLAST_EINVAL;
+    for (int c = 0; c < BLAST_K_CLASSES; c++) {
+        for (auto &ev : p->prof_ev[c]) {
+            cudaEventSynchronize(ev.second);
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
+        p->prof_ev[c].clear();
+        p->prof_ms[c] = 0.0;
+        p->launches[c] = 0;
+    }
+    return BLAST_OK;
 }

@@ -162,12 +162,14 @@ template <class T> static int dev_copy(T **dst, const std::vector<T> &src)
 static void plan_free_device(blast_plan *p)
 {
     void *bufs[] = {p->d_chi, p->d_wchi, p->d_wR, p->d_kcheb_u, p->d_cos_tab, p->d_pref,
-                    p->T64, p->T32, p->Tbf_hi, p->Tbf_lo};
+                    p->T64, p->T32, p->Tsl, p->scT};
     for (void *b : bufs) if (b) cudaFree(b);
     p->d_chi = p->d_wchi = p->d_wR = p->d_kcheb_u = p->d_cos_tab = p->d_pref = nullptr;
-    p->T64 = nullptr; p->T32 = nullptr; p->Tbf_hi = p->Tbf_lo = nullptr;
+    p->T64 = nullptr; p->T32 = nullptr; p->Tsl = nullptr; p->scT = nullptr;
+    if (p->h_err) cudaFreeHost(p->h_err);
+    p->h_err = p->d_err = nullptr;
     p->ws.in.release(); p->ws.coef.release(); p->ws.wts.release();
-    p->ws.ypart.release(); p->ws.cl.release(); p->ws.meta.release();
+    p->ws.ypart.release(); p->ws.cl.release(); p->ws.meta.release(); p->ws.tc.release();
 }
 
 extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
@@ -200,7 +202,7 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
     p->max_clust = d->max_clust; p->max_lens = d->max_lens;
     p->max_tr = d->max_clust > d->max_lens ? d->max_clust : d->max_lens;
     p->device = d->device;
-    p->Nk16 = (p->N + 15) / 16 * 16;
+    p->Kp = (p->N + 63) / 64 * 64;
 
     // chi: uniform nodes, composite Simpson (+ 3/8 panel on the last three
     // intervals when the number of intervals is odd)
@@ -276,6 +278,16 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
         delete p;
         return rc;
     }
+    // error word the kernels' bounded waits write; host mapped so it can be
+    // read without synchronising the stream
+    if (cudaHostAlloc((void **)&p->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&p->d_err, p->h_err, 0) != cudaSuccess) {
+        cudaGetLastError();
+        plan_free_device(p);
+        delete p;
+        return BLAST_EDEVICE;
+    }
+    *p->h_err = 0;
     *out = p;
     return BLAST_OK;
 }
@@ -301,16 +313,16 @@ extern "C" int blast_plan_nodes(const blast_plan *p, double *chi, double *R, dou
 int plan_alloc_basis(blast_plan *p, unsigned mask)
 {
     size_t n64 = (size_t)3 * p->L * p->N * p->Q;
-    size_t nbf = (size_t)3 * p->L * p->Q * p->Nk16;
+    size_t ncol = (size_t)3 * p->L * p->Q;
     if (!p->T64) {
         if (cudaMalloc(&p->T64, n64 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); p->T64 = nullptr; return BLAST_ENOMEM; }
     }
     if ((mask & BLAST_BASIS_FP32) && !p->T32) {
         if (cudaMalloc(&p->T32, n64 * sizeof(float)) != cudaSuccess) { cudaGetLastError(); p->T32 = nullptr; return BLAST_ENOMEM; }
     }
-    if ((mask & BLAST_BASIS_BF16X2) && !p->Tbf_hi) {
-        if (cudaMalloc(&p->Tbf_hi, nbf * 2) != cudaSuccess) { cudaGetLastError(); p->Tbf_hi = nullptr; return BLAST_ENOMEM; }
-        if (cudaMalloc(&p->Tbf_lo, nbf * 2) != cudaSuccess) { cudaGetLastError(); p->Tbf_lo = nullptr; return BLAST_ENOMEM; }
+    if ((mask & BLAST_BASIS_BF16S) && tc_supported(p) && !p->Tsl) {
+        if (cudaMalloc(&p->Tsl, ncol * p->Kp * 2 * BLAST_TC_SLICES) != cudaSuccess) { cudaGetLastError(); p->Tsl = nullptr; return BLAST_ENOMEM; }
+        if (cudaMalloc(&p->scT, ncol * sizeof(float)) != cudaSuccess) { cudaGetLastError(); p->scT = nullptr; return BLAST_ENOMEM; }
     }
     return BLAST_OK;
 }

@@ -5,8 +5,6 @@
 //   T~[t n][l, q] = sum_m A[m][t n] B_l[m][q],  A = w_m f_t(k_m) T_n(x_m),
 //   B_l[m][q]    = j_l(k_m chi_a) j_l(k_m R_r chi_a),
 // with B generated on chip from spherical Bessel recurrences in FP64.
-#include <cuda_bf16.h>
-
 #include <cmath>
 
 #include "blast_internal.h"
@@ -182,39 +180,12 @@ k_basis_gemm(const double *__restrict__ A, const double *__restrict__ kq, int Nk
     }
 }
 
-// FP64 basis -> FP32 copy (same layout) and BF16 hi/lo copies transposed to
-// [t][l][q][Nk16] (Chebyshev index fastest, zero padded): the K-major operand
-// layout of the tensor-core contraction.
+// FP64 basis -> FP32 copy (same layout) for the CUDA-core FP32 path.
 __global__ void k_basis_to_f32(const double *__restrict__ T, float *__restrict__ T32, size_t n)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t stride = (size_t)gridDim.x * blockDim.x;
     for (; i < n; i += stride) T32[i] = (float)T[i];
-}
-
-__global__ void k_basis_to_bf16(const double *__restrict__ T, int N, int Q, int Nk16,
-                                uint16_t *__restrict__ hi, uint16_t *__restrict__ lo)
-{
-    extern __shared__ double tile[];  // [N][64]
-    const int tl = blockIdx.y;        // t*L + e
-    const int q0 = blockIdx.x * 64;
-    const double *src = T + (size_t)tl * N * Q;
-    for (int i = threadIdx.x; i < N * 64; i += blockDim.x) {
-        int n = i / 64, qq = i % 64;
-        tile[i] = (q0 + qq < Q) ? src[(size_t)n * Q + q0 + qq] : 0.0;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64 * Nk16; i += blockDim.x) {
-        int qq = i / Nk16, n = i % Nk16;
-        if (q0 + qq >= Q) continue;
-        double v = (n < N) ? tile[n * 64 + qq] : 0.0;
-        __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-        double rem = v - (double)__bfloat162float(h);
-        __nv_bfloat16 l = __float2bfloat16_rn((float)rem);
-        size_t o = ((size_t)tl * Q + q0 + qq) * Nk16 + n;
-        hi[o] = __bfloat16_as_ushort(h);
-        lo[o] = __bfloat16_as_ushort(l);
-    }
 }
 
 template <int ROWS>
@@ -278,12 +249,9 @@ int launch_basis_convert(blast_plan *p, unsigned mask, cudaStream_t s)
         BL_CUDA(cudaGetLastError());
         p->have32 = true;
     }
-    if ((mask & BLAST_BASIS_BF16X2) && p->Tbf_hi) {
-        size_t smem = sizeof(double) * p->N * 64;
-        BL_CUDA(cudaFuncSetAttribute(k_basis_to_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        dim3 grid((p->Q + 63) / 64, 3 * p->L);
-        k_basis_to_bf16<<<grid, 256, smem, s>>>(p->T64, p->N, p->Q, p->Nk16, p->Tbf_hi, p->Tbf_lo);
-        BL_CUDA(cudaGetLastError());
+    if ((mask & BLAST_BASIS_BF16S) && p->Tsl) {
+        int rc = launch_basis_slices(p, s);
+        if (rc) return rc;
         p->havebf = true;
     }
     return BLAST_OK;
