@@ -184,6 +184,31 @@ int blast_cl(blast_plan *plan, const blast_request *req, int precision,
 int blast_cl_batch(blast_plan *plan, int n, const blast_request *reqs, int precision,
                    double *const *outs, int out_mem_space, void *stream);
 
+/* Allocation-free evaluation.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory while evaluating,
+ * for example a host framework that has reserved the GPU's memory for its own
+ * pool allocator (a cudaMalloc behind its back can fail or fragment the pool)
+ * or a latency-critical request loop (cudaMalloc / cudaFree can synchronise
+ * the device and stall other streams).
+ * It computes the same FP64 C_l as blast_cl(plan, req, BLAST_FP64, ...) but
+ * takes all scratch (coefficients, weights, partial sums, descriptors) from a
+ * fixed device array of BLAST_NOALLOC_SCRATCH_BYTES compiled into the library,
+ * which every GPU that loads the library holds until the process exits.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   req       device inputs only (req->mem_space must be 1), else BLAST_EINVAL
+ *   cl_out    device array [npairs][n_sel], written on the stream
+ *   returns   BLAST_ENOMEM when the request needs more scratch than the array
+ *             holds (about 3 n_ell n_chi max_tracers + (n_clust+n_lens)
+ *             n_chi n_R doubles; the 3x2pt 10+10-bin 100-ell grid fits),
+ *             BLAST_ENOBASIS without an FP64 basis, BLAST_EDEVICE on CUDA errors.
+ * The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array, whose contents persist between calls: every byte a call
+ * reads is written earlier in the same call, and calls that overlap on the GPU
+ * (other streams, other host threads) race on it. */
+#define BLAST_NOALLOC_SCRATCH_BYTES (16u << 20)
+int blast_cl_noalloc(blast_plan *plan, const blast_request *req, double *cl_out, void *stream);
+
 /* Device bytes one request occupies while in flight (inputs, coefficients,
  * weights, partial sums, outputs); the server admits requests against it. */
 size_t blast_request_footprint(const blast_plan *plan, const blast_request *req);

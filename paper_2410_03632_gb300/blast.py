@@ -82,6 +82,7 @@ def lib():
             L.blast_request_footprint.restype = sz
             L.blast_status_str.argtypes = [i]
             L.blast_status_str.restype = ctypes.c_char_p
+            L.blast_cl_noalloc.argtypes = [P, ctypes.POINTER(blast_request), P, P]
             L.blast_profile_enable.argtypes = [P, i]
             L.blast_profile_read.argtypes = [P, i, _dp, ctypes.POINTER(ctypes.c_longlong)]
             L.blast_profile_reset.argtypes = [P]
@@ -130,6 +131,12 @@ def blast_cl_batch(h, reqs, precision, out_ptrs, out_mem_space, stream=None):
     arr = (blast_request * n)(*reqs)
     outs = (_vp * n)(*out_ptrs)
     return lib().blast_cl_batch(h, n, arr, precision, outs, out_mem_space, stream)
+
+
+def blast_cl_noalloc(h, req, out_ptr, stream=None):
+    """FP64 C_l of one cosmology without any device allocation (device inputs
+    and output); scratch comes from a fixed array inside the library."""
+    return lib().blast_cl_noalloc(h, ctypes.byref(req), out_ptr, stream)
 
 
 def blast_request_footprint(h, req):
