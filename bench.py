@@ -338,6 +338,8 @@ def run_blast(args):
         "e2e": {"value": world * B * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "kernels_ms_per_step": {n: prof_main[n][0] / args.steps for n in bl.KERNEL_CLASS_NAMES
+                                if prof_main[n][1]},
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -119,7 +119,7 @@ struct ReqDev {
 int launch_basis(blast_plan *p, cudaStream_t s);
 int launch_basis_convert(blast_plan *p, unsigned mask, cudaStream_t s);
 int launch_fit(blast_plan *p, ReqDev *dreq, int nreq, cudaStream_t s);
-int launch_weights(blast_plan *p, ReqDev *dreq, int nreq, int want32, cudaStream_t s);
+int launch_weights(blast_plan *p, ReqDev *dreq, int nreq, int want32, cudaStream_t s, int want_v64 = 1);
 int launch_contract(blast_plan *p, ReqDev *dreq, int nreq, int prec, const int *d_esel, int n_esel,
                     void *ypart, cudaStream_t s);
 int launch_reduce(blast_plan *p, ReqDev *dreq, int nreq, int prec, const int *d_esel, int n_esel,

@@ -20,9 +20,9 @@
 // in 64-bit integers, W = sum_k D_k 2^(8(4-k)), rounds once to FP32 and scales
 // by 2^(ea + eT - 48).
 //
-// Warp roles (192 threads): warp 0 issues TMA loads of the basis slices,
-// warp 1 owns TMEM and issues tcgen05.mma, warps 2..5 run the epilogue (one
-// TMEM lane = one cosmology per thread).  Every mbarrier wait is bounded; on
+// Warp roles (576 threads): warp 0 issues TMA loads of the basis slices,
+// warp 1 owns TMEM and issues tcgen05.mma, warps 2..17 run the epilogue (one
+// TMEM lane = one cosmology per thread, four warps per lane quadrant).  Every mbarrier wait is bounded; on
 // timeout the kernel records an error code in host-mapped memory and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -38,11 +38,13 @@ constexpr int kS = BLAST_TC_SLICES;       // slices per operand
 constexpr int kQT = 32;                   // chi-R nodes per tile (MMA N)
 constexpr int kM = 128;                   // cosmologies per tile (MMA M)
 constexpr int kKC = 64;                   // K elements per 128-byte swizzle row
-constexpr int kStages = 4;
-constexpr int kThreads = 192;
+constexpr int kStages = 6;
+constexpr int kEP = 4;                    // epilogue warps per TMEM lane quadrant
+constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 16 epilogue warps
+constexpr int kHC = 32 / kEP;             // columns per epilogue thread
 constexpr int kMaxTr = BLAST_MAX_TRACERS / 2;
 constexpr int kNB = 5;                    // B-side tracers handled per thread (registers)
-constexpr uint32_t kASliceBytes = kM * 128;       // 128 rows x 64 bf16
+constexpr uint32_t kACol = 2 * kS * kQT;          // TMEM column of the coefficient slices
 constexpr uint32_t kBSliceBytes = kQT * 128;      // 32 rows x 64 bf16
 constexpr uint32_t kBStageBytes = kS * kBSliceBytes;
 constexpr uint32_t kTmemCols = 512;
@@ -118,14 +120,31 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kQT >> 3) << 17) |
                             ((uint32_t)(kM >> 4) << 24);
 
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t acc)
+// MMA with A read from tensor memory (kM lanes x 16 BF16 packed in 8 columns)
+// and B from shared memory; D += A B when acc != 0, D = A B otherwise.
+__device__ __forceinline__ void umma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bd, uint32_t acc)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "r"(a_tmem), "l"(bd), "r"(kIdesc), "r"(acc));
 }
+
+// Thirty-two consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]),
+        "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void umma_commit(uint64_t *bar)
 {
@@ -140,6 +159,43 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4])
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(taddr));
+}
+
+// Knuth's two-sum: s + e == a + b exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    const float ss = __fadd_rn(a, b);
+    const float bb = __fsub_rn(ss, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(ss, bb)), __fsub_rn(b, bb));
+    s = ss;
+}
+
+// Fast two-sum (|a| >= |b| or a == 0): s + e == a + b exactly.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    const float ss = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(ss, a));
+    s = ss;
+}
+
+// Exact float of an integer x < 2^23: x placed in the mantissa of 2^23, minus 2^23.
+__device__ __forceinline__ float u23_to_float(unsigned x)
+{
+    return __fsub_rn(__uint_as_float(0x4B000000u | x), 8388608.0f);
+}
+
+// x < 2^56 as h + l (h = x rounded to float, l the exact remainder as a float):
+// x = c2 2^46 + c1 2^23 + c0 with 23-bit pieces, each exact, summed by fast two-sums.
+__device__ __forceinline__ void split_u56(unsigned long long x, float &h, float &l)
+{
+    const float f0 = u23_to_float((unsigned)(x & 0x7FFFFFull));
+    const float f1 = __fmul_rn(u23_to_float((unsigned)((x >> 23) & 0x7FFFFFull)), 8388608.0f);
+    const float f2 = __fmul_rn(u23_to_float((unsigned)(x >> 46)), 70368744177664.0f);  // 2^46
+    float s1, e1, s2, e2;
+    fast_two_sum(f2, f1, s1, e1);
+    fast_two_sum(s1, f0, s2, e2);
+    h = s2;
+    l = __fadd_rn(e1, e2);
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -159,9 +215,10 @@ __device__ __forceinline__ void slice8(double xn, uint16_t (&out)[kS])
     }
 }
 
-// Coefficient slices, one warp per cosmology: A_p[b][n] and 2^ea(b).
+// Coefficient slices, one warp per cosmology: A_p[b][n] and 2^ea(b); also the
+// chi weights U transposed to cosmology-fastest order for the reduction.
 __global__ void k_coef_slices(const ReqDev *__restrict__ reqs, int n, int N, int Kp, int Bpad, uint16_t *A,
-                              float *sa)
+                              float *sa, int X, int ntr_max, float *UT, float *UTl)
 {
     const int b = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
     if (b >= Bpad) return;
@@ -179,6 +236,14 @@ __global__ void k_coef_slices(const ReqDev *__restrict__ reqs, int n, int N, int
         for (int p = 0; p < kS; p++) A[((size_t)p * Bpad + b) * Kp + k] = s[p];
     }
     if (lane == 0) sa[b] = ldexpf(1.0f, e);
+    const int ntr = (b < n) ? reqs[b].n_clust + reqs[b].n_lens : 0;
+    const double *U = (b < n) ? reqs[b].U64 : nullptr;
+    for (int i = lane; i < ntr_max * X; i += 32) {
+        const double u = (i < ntr * X) ? U[i] : 0.0;
+        const float uh = (float)u;
+        UT[(size_t)i * Bpad + b] = uh;
+        UTl[(size_t)i * Bpad + b] = (float)(u - (double)uh);
+    }
 }
 
 // Basis slices, one thread per column (t, l, q): T_p[col][n] and 2^(eT - 16 - 8(S-1)).
@@ -211,22 +276,23 @@ struct TcArgs {
     const int *esel;
     const float *scT;    // [3][L][Q]
     const float *sa;     // [Bpad]
+    const uint16_t *A;   // [S][Bpad][64] coefficient slices
     float *Y;            // [3][n_esel][X][RT][MT][n]  (cosmology fastest)
     int *err;            // host-mapped error word
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-k_contract_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs args)
+k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA = smem;                                  // kS x 16 KB
-    unsigned char *sB = smem + kS * kASliceBytes;              // kStages x kS x 4 KB
+    unsigned char *sB = smem;                                  // kStages x kS x 4 KB
     uint64_t *bars = (uint64_t *)(sB + kStages * kBStageBytes);
-    uint64_t *full = bars, *empty = bars + kStages, *afull = bars + 2 * kStages;
-    uint64_t *tfull = afull + 1, *tempty = tfull + 2;
-    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
+    uint64_t *full = bars, *empty = bars + kStages, *aready = bars + 2 * kStages;
+    uint64_t *tfull = aready + 1, *tempty = tfull + 2, *yfull = tempty + 2, *yempty = yfull + 2;
+    float *ybuf = (float *)(yempty + 2);                      // [2][kEP-1][kM][2 kNB] partial pairs
+    uint32_t *tmem_slot = (uint32_t *)(ybuf + 2 * (kEP - 1) * kM * 2 * kNB);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -235,8 +301,11 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; i++) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        mbar_init(afull, 1);
-        for (int i = 0; i < 2; i++) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128); }
+        mbar_init(aready, 128);
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128 * kEP);
+            mbar_init(&yfull[i], 128 * (kEP - 1)); mbar_init(&yempty[i], 128);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -252,10 +321,6 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer (whole warp waits, lane 0 issues)
-        if (lane == 0) {
-            mbar_expect_tx(afull, kS * kASliceBytes);
-            tma_load_3d(sA, &mapA, afull, 0, btile * kM, 0);
-        }
         uint32_t g = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < args.nbt * args.nqt; u += gridDim.x) {
@@ -280,13 +345,13 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         // drain: every issued load has landed before the CTA may exit
         for (uint32_t h = (g > kStages ? g - kStages : 0); h < g; h++)
             mbar_wait(&full[h % kStages], (h / kStages) & 1);
-        mbar_wait(afull, 0);
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (whole warp waits, lane 0 issues)
-        bool ok = mbar_wait(afull, 0);
+        bool ok = mbar_wait(aready, 0);  // coefficient slices written into TMEM by the epilogue
         if (!ok && lane == 0) { atomicExch(args.err, 2); *abort_flag = 1; }
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        tc_fence_after();
+        const uint32_t b0 = smem_u32(sB);
         uint32_t g = 0;
         for (int u = blockIdx.x; ok && u < args.nbt * args.nqt; u += gridDim.x) {
             for (int it = 0; it < n_iter_unit; it++, g++) {
@@ -310,9 +375,9 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                             const int q = lev - p;
 #pragma unroll
                             for (int kk = 0; kk < kKC / 16; kk++) {
-                                const uint64_t ad = sdesc(a0 + p * kASliceBytes + kk * 32);
+                                const uint32_t at = tmem + kACol + p * (kKC / 2) + kk * 8;
                                 const uint64_t bd = sdesc(bst + q * kBSliceBytes + kk * 32);
-                                umma(dbase + lev * kQT, ad, bd, (p > 0 || kk > 0) ? 1u : 0u);
+                                umma_ts(dbase + lev * kQT, at, bd, (p > 0 || kk > 0) ? 1u : 0u);
                             }
                         }
                     }
@@ -323,33 +388,56 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             }
         }
     } else {
-        // ------------------------------------------------ epilogue: one cosmology per thread
-        const int quad = warp & 3;
+        // ------------------------------------------------ epilogue: kEP warps per TMEM lane quadrant;
+        // a thread owns one cosmology (TMEM lane) and kHC of the tile's 32 columns.
+        const int ew = warp - 2;
+        const int quad = warp & 3;   // lanes 32 quad .. 32 quad + 31 are readable by this warp
+        const int part = ew >> 2;    // columns [kHC part, kHC part + kHC)
         const int bl_ = quad * 32 + lane;
         const int b = btile * kM + bl_;
         const bool valid = b < args.n;
         const ReqDev *rq = valid ? &args.reqs[b] : nullptr;
         const int ng = valid ? rq->n_clust : 0, ns = valid ? rq->n_lens : 0;
-        const float sa = args.sa[b < args.Bpad ? b : 0];
+        const float sa = args.sa[b];
         const uint32_t lane_addr = ((uint32_t)(quad * 32)) << 16;
+        const int cb = part * kHC;
+        if (part == 0) {
+            // coefficient slices of cosmology b -> TMEM lane b, columns kACol + 32 p ..
+#pragma unroll 1
+            for (int p = 0; p < kS; p++) {
+                uint32_t r[32];
+                const uint4 *src = reinterpret_cast<const uint4 *>(args.A + ((size_t)p * args.Bpad + b) * kKC);
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const uint4 v = __ldg(src + i);
+                    r[4 * i] = v.x; r[4 * i + 1] = v.y; r[4 * i + 2] = v.z; r[4 * i + 3] = v.w;
+                }
+                tmem_st32(tmem + lane_addr + kACol + p * (kKC / 2), r);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            mbar_arrive(aready);
+        }
         uint32_t g = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < args.nbt * args.nqt; u += gridDim.x) {
             const int q0 = (u / args.nbt) * kQT;
             const int a = q0 / args.Rn, rt = (q0 % args.Rn) / kQT;
-            float wv[kNB][kQT];
+            float wv[kNB][kHC];  // quadrature weights of this cosmology, times its scale 2^ea
             for (int t = 0; t < 3 && ok; t++) {
                 const int offB = (t == 0) ? 0 : ng, nB = (t == 0) ? ng : ns;
                 if (t < 2) {
 #pragma unroll
                     for (int j = 0; j < kNB; j++) {
-                        const float4 *src = (valid && j < nB)
-                                                ? reinterpret_cast<const float4 *>(rq->V32 + (size_t)(offB + j) * args.Q + q0)
-                                                : nullptr;
+                        const float4 *src =
+                            (valid && j < nB)
+                                ? reinterpret_cast<const float4 *>(rq->V32 + (size_t)(offB + j) * args.Q + q0 + cb)
+                                : nullptr;
 #pragma unroll
-                        for (int c = 0; c < kQT / 4; c++) {
+                        for (int c = 0; c < kHC / 4; c++) {
                             float4 v = src ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-                            wv[j][4 * c] = v.x; wv[j][4 * c + 1] = v.y; wv[j][4 * c + 2] = v.z; wv[j][4 * c + 3] = v.w;
+                            wv[j][4 * c] = v.x * sa; wv[j][4 * c + 1] = v.y * sa;
+                            wv[j][4 * c + 2] = v.z * sa; wv[j][4 * c + 3] = v.w * sa;
                         }
                     }
                 }
@@ -359,36 +447,91 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     if (!mbar_wait(&tfull[buf], tph)) { atomicExch(args.err, 4); ok = false; break; }
                     tc_fence_after();
                     const int e = args.esel[es];
-                    const float *sc = args.scT + ((size_t)t * args.L + e) * args.Q + q0;
-                    float Yj[kNB];
+                    const float *sc = args.scT + ((size_t)t * args.L + e) * args.Q + q0 + cb;
+                    // R-sum of this thread's columns as an unevaluated pair (Sh + Sl): each
+                    // product V w is split exactly (FMA) and each addition's rounding error
+                    // is kept (two-sum), so the sum survives the cancellation of oscillating w
+                    float Sh[kNB], Sl[kNB];
 #pragma unroll
-                    for (int j = 0; j < kNB; j++) Yj[j] = 0.f;
+                    for (int j = 0; j < kNB; j++) { Sh[j] = 0.f; Sl[j] = 0.f; }
 #pragma unroll
-                    for (int c0 = 0; c0 < kQT; c0 += 4) {
+                    for (int c0 = 0; c0 < kHC; c0 += 4) {
                         uint32_t D[kS][4];
 #pragma unroll
                         for (int lev = 0; lev < kS; lev++)
-                            tmem_ld4(tmem + lane_addr + buf * (kS * kQT) + lev * kQT + c0, D[lev]);
+                            tmem_ld4(tmem + lane_addr + buf * (kS * kQT) + lev * kQT + cb + c0, D[lev]);
+                        const float4 s4 = __ldg(reinterpret_cast<const float4 *>(sc + c0));
+                        const float scv[4] = {s4.x, s4.y, s4.z, s4.w};
                         tmem_wait_ld();
+                        if (c0 + 4 == kHC) {  // every level of this buffer is in registers: release it
+                            tc_fence_before();
+                            mbar_arrive(&tempty[buf]);
+                        }
 #pragma unroll
                         for (int c = 0; c < 4; c++) {
-                            long long W = (long long)__float2int_rn(__uint_as_float(D[0][c]));
+                            // exact: W = sum_k D_k 2^(8(4-k)) with |D_0| <= 2^22, |D_k| < 2^23 (K <= 64),
+                            // so both 32-bit partial words fit without overflow
+                            const int d0 = __float2int_rn(__uint_as_float(D[0][c]));
+                            const int d1 = __float2int_rn(__uint_as_float(D[1][c]));
+                            const int d2 = __float2int_rn(__uint_as_float(D[2][c]));
+                            const int d3 = __float2int_rn(__uint_as_float(D[3][c]));
+                            const int d4 = __float2int_rn(__uint_as_float(D[4][c]));
+                            const int hi = d0 * 256 + d1, mid = d2 * 256 + d3;
+                            const long long W = ((long long)hi << 24) + ((long long)mid << 8) + d4;
+                            // |W| < 2^56 as an exact pair wh + wl of floats, from three 23-bit pieces
+                            // converted exactly without conversion instructions (a 64-bit
+                            // conversion would run on the FP64 pipe)
+                            const unsigned long long Aw = (unsigned long long)(W < 0 ? -W : W);
+                            float wh, wl;
+                            split_u56(Aw, wh, wl);
+                            const float sgn = (W < 0) ? -scv[c] : scv[c];
+                            wh = __fmul_rn(wh, sgn);
+                            wl = __fmul_rn(wl, sgn);
 #pragma unroll
-                            for (int lev = 1; lev < kS; lev++)
-                                W = W * 256 + (long long)__float2int_rn(__uint_as_float(D[lev][c]));
-                            const float w = (__ll2float_rn(W) * sa) * __ldg(sc + c0 + c);
-#pragma unroll
-                            for (int j = 0; j < kNB; j++) Yj[j] = fmaf(wv[j][c0 + c], w, Yj[j]);
+                            for (int j = 0; j < kNB; j++) {
+                                const float v = wv[j][c0 + c];
+                                const float pr = __fmul_rn(v, wh);
+                                const float pe = fmaf(v, wl, fmaf(v, wh, -pr));
+                                float se;
+                                two_sum(Sh[j], pr, Sh[j], se);
+                                Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, pe));
+                            }
                         }
                     }
-                    tc_fence_before();
-                    mbar_arrive(&tempty[buf]);
-                    if (valid) {
-                        float *y = args.Y + ((((size_t)t * args.n_esel + es) * (args.Q / args.Rn) + a) * args.RT + rt) *
-                                                (size_t)args.MT * args.n + b;
+                    // add the column parts: parts 1.. hand their pairs to part 0
+                    const int yb = g & 1;
+                    const uint32_t yph = (g >> 1) & 1;
+                    if (part > 0) {
+                        float *slot = ybuf + (((size_t)yb * (kEP - 1) + part - 1) * kM + bl_) * (2 * kNB);
+                        if (!mbar_wait(&yempty[yb], yph ^ 1)) { atomicExch(args.err, 5); ok = false; break; }
 #pragma unroll
-                        for (int j = 0; j < kNB; j++)
-                            if (j < args.MT) y[(size_t)j * args.n] = Yj[j];
+                        for (int j = 0; j < kNB; j++) { slot[j] = Sh[j]; slot[kNB + j] = Sl[j]; }
+                        mbar_arrive(&yfull[yb]);
+                    } else {
+                        if (!mbar_wait(&yfull[yb], yph)) { atomicExch(args.err, 6); ok = false; break; }
+#pragma unroll
+                        for (int q = 0; q < kEP - 1; q++) {
+                            const float *slot = ybuf + (((size_t)yb * (kEP - 1) + q) * kM + bl_) * (2 * kNB);
+#pragma unroll
+                            for (int j = 0; j < kNB; j++) {
+                                float se;
+                                two_sum(Sh[j], slot[j], Sh[j], se);
+                                Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, slot[kNB + j]));
+                            }
+                        }
+                        mbar_arrive(&yempty[yb]);
+                        if (valid) {
+                            // pair (hi, lo) of tracer j at j and MT + j
+                            float *y = args.Y +
+                                       ((((size_t)t * args.n_esel + es) * (args.Q / args.Rn) + a) * args.RT + rt) *
+                                           (size_t)(2 * args.MT) * args.n + b;
+#pragma unroll
+                            for (int j = 0; j < kNB; j++)
+                                if (j < args.MT) {
+                                    y[(size_t)j * args.n] = Sh[j];
+                                    y[(size_t)(args.MT + j) * args.n] = Sl[j];
+                                }
+                        }
                     }
                 }
             }
@@ -405,7 +548,8 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 // Sum over R-tiles and chi nodes for the tensor-core path, FP32, one thread per
 // (cosmology, type, ell, B-side tracer j) accumulating every A-side tracer i:
 //   C_ij(l) = N_AB(l) sum_a U_i(a) sum_rt Y(t, l, a, rt, j)
-__global__ void k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, int n, int X, int L,
+__global__ void k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const float *__restrict__ UT,
+                            const float *__restrict__ UTl, int n, int Bpad, int X, int L,
                             const int *__restrict__ esel, int n_esel, int RT, int MT, const double *__restrict__ pref)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -418,16 +562,32 @@ __global__ void k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__rest
     const int e = esel[es];
     const int col = rq.e_out[e];
     if (col < 0) return;
-    float Z[kMaxTr];
+    float Zh[kMaxTr], Zl[kMaxTr];
 #pragma unroll
-    for (int i = 0; i < kMaxTr; i++) Z[i] = 0.f;
-    const float *Yp = Y + ((size_t)t * n_esel + es) * (size_t)X * RT * MT * n + (size_t)j * n + b;
+    for (int i = 0; i < kMaxTr; i++) { Zh[i] = 0.f; Zl[i] = 0.f; }
+    const float *Yp = Y + ((size_t)t * n_esel + es) * (size_t)X * RT * 2 * MT * n + (size_t)j * n + b;
     for (int a = 0; a < X; a++) {
-        float s = 0.f;
-        for (int rt = 0; rt < RT; rt++) s += Yp[((size_t)a * RT + rt) * MT * n];
+        // R-tile pairs (hi at j, lo at MT + j) summed with two-sum, then rounded once
+        float sh = 0.f, sl = 0.f;
+        for (int rt = 0; rt < RT; rt++) {
+            const float *yy = Yp + ((size_t)a * RT + rt) * 2 * MT * n;
+            float se;
+            two_sum(sh, yy[0], sh, se);
+            sl = __fadd_rn(sl, __fadd_rn(se, yy[(size_t)MT * n]));
+        }
+        float s, sle;
+        two_sum(sh, sl, s, sle);  // renormalised pair (s, sle)
 #pragma unroll
         for (int i = 0; i < kMaxTr; i++)
-            if (i < nA) Z[i] = fmaf(rq.U32[(size_t)(offA + i) * X + a], s, Z[i]);
+            if (i < nA) {
+                const size_t ui = ((size_t)(offA + i) * X + a) * Bpad + b;
+                const float uh = UT[ui], ul = UTl[ui];
+                const float pr = __fmul_rn(uh, s);
+                const float pe = fmaf(uh, sle, fmaf(ul, s, fmaf(uh, s, -pr)));
+                float se;
+                two_sum(Zh[i], pr, Zh[i], se);
+                Zl[i] = __fadd_rn(Zl[i], __fadd_rn(se, pe));
+            }
     }
     const double pf = pref[t * L + e];
     const int ngg = ng * (ng + 1) / 2, ngs = ng * ns;
@@ -436,7 +596,7 @@ __global__ void k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__rest
         if (t == 0) { if (i > j) continue; p = i * ng - i * (i - 1) / 2 + (j - i); }
         else if (t == 1) p = ngg + i * ns + j;
         else { if (i > j) continue; p = ngg + ngs + i * ns - i * (i - 1) / 2 + (j - i); }
-        double out = pf * (double)Z[i];
+        double out = pf * ((double)Zh[i] + (double)Zl[i]);
         if (rq.status) out = nan("");
         rq.cl[(size_t)p * rq.n_sel + col] = out;
     }
@@ -480,7 +640,14 @@ int make_map(CUtensorMap *m, void *base, int Kp, long long rows, int box_rows)
     return BLAST_OK;
 }
 
-size_t tc_smem_bytes() { return 1024 + kS * kASliceBytes + kStages * kBStageBytes + 256; }
+// Work space of one tensor-core call: coefficient slices, scales, transposed U.
+size_t tc_ws_bytes(const blast_plan *p, int Bpad)
+{
+    return (size_t)kS * Bpad * p->Kp * 2 + (size_t)Bpad * 4 +
+           2 * (size_t)(p->max_clust + p->max_lens) * p->X * Bpad * 4 + 256;
+}
+
+size_t tc_smem_bytes() { return 1024 + kStages * kBStageBytes + 256 + 2 * (kEP - 1) * kM * 2 * kNB * 4; }
 
 }  // namespace
 
@@ -503,14 +670,16 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     Workspace &ws = p->ws;
     const int Bpad = (n + kM - 1) / kM * kM;
     int rc;
-    if ((rc = ws.tc.ensure((size_t)kS * Bpad * p->Kp * 2 + (size_t)Bpad * 4 + 256))) return rc;
+    const int ntr_max = p->max_clust + p->max_lens;
+    if ((rc = ws.tc.ensure(tc_ws_bytes(p, Bpad)))) return rc;
     uint16_t *A = ws.tc.as<uint16_t>();
     float *sa = reinterpret_cast<float *>(A + (size_t)kS * Bpad * p->Kp);
-    k_coef_slices<<<Bpad / 8, 256, 0, s>>>(dreq, n, p->N, p->Kp, Bpad, A, sa);
+    float *UT = sa + Bpad;
+    float *UTl = UT + (size_t)ntr_max * p->X * Bpad;
+    k_coef_slices<<<Bpad / 8, 256, 0, s>>>(dreq, n, p->N, p->Kp, Bpad, A, sa, p->X, ntr_max, UT, UTl);
     BL_CUDA(cudaGetLastError());
 
-    CUtensorMap mapA, mapB;
-    if ((rc = make_map(&mapA, A, p->Kp, Bpad, kM))) return rc;
+    CUtensorMap mapB;
     if ((rc = make_map(&mapB, p->Tsl, p->Kp, (long long)3 * p->L * p->Q, kQT))) return rc;
     TcArgs args;
     args.reqs = dreq;
@@ -527,6 +696,7 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     args.esel = d_esel;
     args.scT = p->scT;
     args.sa = sa;
+    args.A = A;
     args.Y = (float *)ypart;
     args.err = p->d_err;
     int sms = 0;
@@ -537,7 +707,7 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     if (grid < args.nbt) grid = args.nbt;
     size_t smem = tc_smem_bytes();
     BL_CUDA(cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_contract_tc<<<grid, kThreads, smem, s>>>(mapA, mapB, args);
+    k_contract_tc<<<grid, kThreads, smem, s>>>(mapB, args);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
 }
@@ -545,9 +715,12 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
 int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int n_esel, const void *ypart,
                      cudaStream_t s)
 {
+    const int Bpad = (n + kM - 1) / kM * kM;
+    const float *UT = reinterpret_cast<const float *>(p->ws.tc.as<uint16_t>() + (size_t)kS * Bpad * p->Kp) + Bpad;
+    const float *UTl = UT + (size_t)(p->max_clust + p->max_lens) * p->X * Bpad;
     dim3 grid((n + 127) / 128, n_esel * p->max_tr, 3);
-    k_reduce_tc<<<grid, 128, 0, s>>>(dreq, (const float *)ypart, n, p->X, p->L, d_esel, n_esel, p->Rn / kQT,
-                                     p->max_tr, p->d_pref);
+    k_reduce_tc<<<grid, 128, 0, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel, n_esel,
+                                     p->Rn / kQT, p->max_tr, p->d_pref);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
 }

@@ -130,14 +130,14 @@ k_fit(ReqDev *reqs, int N, const double *__restrict__ node_u, const double *__re
 //   V[tr][q] = wR_r D(R_r chi_a) K_tr(R_r chi_a),   q = a n_R + r
 // ---------------------------------------------------------------------------
 __global__ void k_weights(ReqDev *reqs, int X, int Rn, const double *__restrict__ chi,
-                          const double *__restrict__ wchi, const double *__restrict__ wR, int want32)
+                          const double *__restrict__ wchi, const double *__restrict__ wR, int want32, int want_v64)
 {
     ReqDev &rq = reqs[blockIdx.y];
     const int ntr = rq.n_clust + rq.n_lens, Q = X * Rn;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntr * Q; i += gridDim.x * blockDim.x) {
         int q = i % Q, r = q % Rn;
         double vv = wR[r] * rq.growth_Rchi[q] * rq.kern_Rchi[i];
-        rq.V64[i] = vv;
+        if (want_v64) rq.V64[i] = vv;
         if (want32) rq.V32[i] = (float)vv;
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntr * X; i += gridDim.x * blockDim.x) {
@@ -244,10 +244,10 @@ int launch_fit(blast_plan *p, ReqDev *dreq, int nreq, cudaStream_t s)
     return BLAST_OK;
 }
 
-int launch_weights(blast_plan *p, ReqDev *dreq, int nreq, int want32, cudaStream_t s)
+int launch_weights(blast_plan *p, ReqDev *dreq, int nreq, int want32, cudaStream_t s, int want_v64)
 {
     dim3 grid((p->Q * 2 + 255) / 256 < 1024 ? (p->Q * 2 + 255) / 256 : 1024, nreq);
-    k_weights<<<grid, 256, 0, s>>>(dreq, p->X, p->Rn, p->d_chi, p->d_wchi, p->d_wR, want32);
+    k_weights<<<grid, 256, 0, s>>>(dreq, p->X, p->Rn, p->d_chi, p->d_wchi, p->d_wR, want32, want_v64);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
 }
@@ -423,7 +423,7 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
     BL_CUDA(cudaMemcpyAsync(dreq, hreq.data(), sizeof(ReqDev) * n, cudaMemcpyHostToDevice, s));
     BL_CUDA(cudaMemcpyAsync(de, esel.data(), sizeof(int) * esel.size(), cudaMemcpyHostToDevice, s));
     if ((rc = prof_launch(p, BLAST_K_FIT, s, [&] { return launch_fit(p, dreq, n, s); }))) return rc;
-    if ((rc = prof_launch(p, BLAST_K_WEIGHTS, s, [&] { return launch_weights(p, dreq, n, prec != BLAST_FP64, s); }))) return rc;
+    if ((rc = prof_launch(p, BLAST_K_WEIGHTS, s, [&] { return launch_weights(p, dreq, n, prec != BLAST_FP64, s, prec == BLAST_FP64); }))) return rc;
     *dreq_out = dreq;
     *d_esel = de;
     return BLAST_OK;
@@ -469,7 +469,7 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
     int rc = stage_batch(p, n, reqs, prec, outs, out_mem_space, s, &dreq, &d_esel, &n_esel, hreq);
     if (rc) return rc;
     if (use_tc) {
-        const size_t ybytes = (size_t)n * 3 * n_esel * p->X * (p->Rn / 32) * p->max_tr * 4;
+        const size_t ybytes = (size_t)n * 3 * n_esel * p->X * (p->Rn / 32) * 2 * p->max_tr * 4;
         if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
         if ((rc = prof_launch(p, BLAST_K_CONTRACT_TC, s, [&] {
                  return launch_contract_tc(p, dreq, n, d_esel, n_esel, p->ws.ypart.p, s);
