@@ -17,13 +17,17 @@
 // exact, and each level D_k = sum_{p+q=k} sum_n A_p T_q stays below 2^24, so
 // the FP32 tensor-core accumulation is exact.  The 15 slice pairs p+q <= 4
 // feed 5 level accumulators in TMEM; the epilogue combines the levels exactly
-// in 64-bit integers, W = sum_k D_k 2^(8(4-k)), rounds once to FP32 and scales
-// by 2^(ea + eT - 48).
+// in 64-bit integers, W = sum_k D_k 2^(8(4-k)), turns W into an exact pair of
+// floats and scales by 2^(ea + eT - 48).  The R sum that follows also cancels
+// (w oscillates around R = 1), so it runs on unevaluated pairs: exact
+// products (FMA) and two-sum accumulation; the pairs reach the chi sum intact.
 //
 // Warp roles (576 threads): warp 0 issues TMA loads of the basis slices,
-// warp 1 owns TMEM and issues tcgen05.mma, warps 2..17 run the epilogue (one
-// TMEM lane = one cosmology per thread, four warps per lane quadrant).  Every mbarrier wait is bounded; on
-// timeout the kernel records an error code in host-mapped memory and exits.
+// warp 1 owns TMEM and issues tcgen05.mma (A = coefficient slices resident in
+// TMEM, B = basis slices in shared memory), warps 2..17 run the epilogue (one
+// TMEM lane = one cosmology per thread, four warps per lane quadrant).  Every
+// mbarrier wait is bounded; on timeout the kernel records an error code in
+// host-mapped memory and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -42,7 +46,6 @@ constexpr int kStages = 6;
 constexpr int kEP = 4;                    // epilogue warps per TMEM lane quadrant
 constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 16 epilogue warps
 constexpr int kHC = 32 / kEP;             // columns per epilogue thread
-constexpr int kMaxTr = BLAST_MAX_TRACERS / 2;
 constexpr int kNB = 5;                    // B-side tracers handled per thread (registers)
 constexpr uint32_t kACol = 2 * kS * kQT;          // TMEM column of the coefficient slices
 constexpr uint32_t kBSliceBytes = kQT * 128;      // 32 rows x 64 bf16
@@ -545,60 +548,122 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     }
 }
 
-// Sum over R-tiles and chi nodes for the tensor-core path, FP32, one thread per
-// (cosmology, type, ell, B-side tracer j) accumulating every A-side tracer i:
-//   C_ij(l) = N_AB(l) sum_a U_i(a) sum_rt Y(t, l, a, rt, j)
-__global__ void k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const float *__restrict__ UT,
-                            const float *__restrict__ UTl, int n, int Bpad, int X, int L,
-                            const int *__restrict__ esel, int n_esel, int RT, int MT, const double *__restrict__ pref)
+// Sum over R tiles and chi nodes for the tensor-core path, one thread per
+// (cosmology, type, ell) accumulating every tracer pair (i, j):
+//   s_j(a) = sum_rt Y(t, l, a, rt, j)          (pairs (hi, lo), two-sum)
+//   C_ij(l) = N_AB(l) sum_a U_i(a) s_j(a)      (exact products, two-sum)
+constexpr int kRedChunks = 8;  // chi chunks per (cosmology, type, ell): one warp each
+constexpr int kRedRT = 2;      // R tiles whose loads are issued together
+
+__global__ void __launch_bounds__(32 * kRedChunks, 2)
+k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const float *__restrict__ UT,
+            const float *__restrict__ UTl, int n, int Bpad, int X, int L, const int *__restrict__ esel, int n_esel,
+            int RT, int MT, const double *__restrict__ pref)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y % MT, es = blockIdx.y / MT, t = blockIdx.z;
-    if (b >= n) return;
-    const ReqDev &rq = reqs[b];
-    const int ng = rq.n_clust, ns = rq.n_lens;
+    __shared__ float red[kRedChunks / 2][32][2 * kNB * kNB];
+    const int lane = threadIdx.x & 31, chunk = threadIdx.x >> 5;
+    const int b = blockIdx.x * 32 + lane;
+    const int es = blockIdx.y, t = blockIdx.z;
+    const ReqDev *rq = (b < n) ? &reqs[b] : nullptr;
+    const int ng = rq ? rq->n_clust : 0, ns = rq ? rq->n_lens : 0;
     const int nA = (t == 2) ? ns : ng, nB = (t == 0) ? ng : ns, offA = (t == 2) ? ng : 0;
-    if (j >= nB || nA == 0) return;
     const int e = esel[es];
-    const int col = rq.e_out[e];
-    if (col < 0) return;
-    float Zh[kMaxTr], Zl[kMaxTr];
+    const int col = rq ? rq->e_out[e] : -1;
+    const bool active = rq && nA > 0 && nB > 0 && col >= 0;
+    float Zh[kNB][kNB], Zl[kNB][kNB];
 #pragma unroll
-    for (int i = 0; i < kMaxTr; i++) { Zh[i] = 0.f; Zl[i] = 0.f; }
-    const float *Yp = Y + ((size_t)t * n_esel + es) * (size_t)X * RT * 2 * MT * n + (size_t)j * n + b;
-    for (int a = 0; a < X; a++) {
-        // R-tile pairs (hi at j, lo at MT + j) summed with two-sum, then rounded once
-        float sh = 0.f, sl = 0.f;
-        for (int rt = 0; rt < RT; rt++) {
-            const float *yy = Yp + ((size_t)a * RT + rt) * 2 * MT * n;
-            float se;
-            two_sum(sh, yy[0], sh, se);
-            sl = __fadd_rn(sl, __fadd_rn(se, yy[(size_t)MT * n]));
-        }
-        float s, sle;
-        two_sum(sh, sl, s, sle);  // renormalised pair (s, sle)
+    for (int i = 0; i < kNB; i++)
 #pragma unroll
-        for (int i = 0; i < kMaxTr; i++)
-            if (i < nA) {
-                const size_t ui = ((size_t)(offA + i) * X + a) * Bpad + b;
-                const float uh = UT[ui], ul = UTl[ui];
-                const float pr = __fmul_rn(uh, s);
-                const float pe = fmaf(uh, sle, fmaf(ul, s, fmaf(uh, s, -pr)));
-                float se;
-                two_sum(Zh[i], pr, Zh[i], se);
-                Zl[i] = __fadd_rn(Zl[i], __fadd_rn(se, pe));
+        for (int j = 0; j < kNB; j++) { Zh[i][j] = 0.f; Zl[i][j] = 0.f; }
+    const size_t ystride = (size_t)n;  // between tracer slots
+    const float *Yp = Y + ((size_t)t * n_esel + es) * (size_t)X * RT * 2 * MT * n + b;
+    const int per = (X + kRedChunks - 1) / kRedChunks;
+    const int a0 = chunk * per, a1 = min(X, a0 + per);
+    for (int a = a0; active && a < a1; a++) {
+        float sh[kNB], sl[kNB];
+#pragma unroll
+        for (int j = 0; j < kNB; j++) { sh[j] = 0.f; sl[j] = 0.f; }
+        // kRedRT R tiles per round, every load of the round issued before the sums
+        for (int rt0 = 0; rt0 < RT; rt0 += kRedRT) {
+            float v[kRedRT][2 * kNB];
+#pragma unroll
+            for (int k = 0; k < kRedRT; k++) {
+                const bool ok = rt0 + k < RT;
+                const float *yy = Yp + ((size_t)a * RT + rt0 + k) * 2 * MT * ystride;
+#pragma unroll
+                for (int j = 0; j < kNB; j++) {
+                    v[k][j] = (ok && j < nB) ? __ldg(yy + (size_t)j * ystride) : 0.f;
+                    v[k][kNB + j] = (ok && j < nB) ? __ldg(yy + (size_t)(MT + j) * ystride) : 0.f;
+                }
             }
+#pragma unroll
+            for (int k = 0; k < kRedRT; k++)
+#pragma unroll
+                for (int j = 0; j < kNB; j++) {
+                    float se;
+                    two_sum(sh[j], v[k][j], sh[j], se);
+                    sl[j] = __fadd_rn(sl[j], __fadd_rn(se, v[k][kNB + j]));
+                }
+        }
+        float sv[kNB], sle[kNB];
+#pragma unroll
+        for (int j = 0; j < kNB; j++) two_sum(sh[j], sl[j], sv[j], sle[j]);
+#pragma unroll
+        for (int i = 0; i < kNB; i++) {
+            if (i >= nA) continue;
+            const size_t ui = ((size_t)(offA + i) * X + a) * Bpad + b;
+            const float uh = UT[ui], ul = UTl[ui];
+#pragma unroll
+            for (int j = 0; j < kNB; j++) {
+                if (j >= nB) continue;
+                const float pr = __fmul_rn(uh, sv[j]);
+                const float pe = fmaf(uh, sle[j], fmaf(ul, sv[j], fmaf(uh, sv[j], -pr)));
+                float se;
+                two_sum(Zh[i][j], pr, Zh[i][j], se);
+                Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, pe));
+            }
+        }
     }
+    // tree over the chi chunks: the upper half of the warps hands its pairs down
+    for (int half = kRedChunks / 2; half >= 1; half >>= 1) {
+        if (chunk >= half && chunk < 2 * half) {
+#pragma unroll
+            for (int i = 0; i < kNB; i++)
+#pragma unroll
+                for (int j = 0; j < kNB; j++) {
+                    red[chunk - half][lane][2 * (i * kNB + j)] = Zh[i][j];
+                    red[chunk - half][lane][2 * (i * kNB + j) + 1] = Zl[i][j];
+                }
+        }
+        __syncthreads();
+        if (chunk < half) {
+#pragma unroll
+            for (int i = 0; i < kNB; i++)
+#pragma unroll
+                for (int j = 0; j < kNB; j++) {
+                    float se;
+                    two_sum(Zh[i][j], red[chunk][lane][2 * (i * kNB + j)], Zh[i][j], se);
+                    Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, red[chunk][lane][2 * (i * kNB + j) + 1]));
+                }
+        }
+        __syncthreads();
+    }
+    if (chunk != 0 || !active) return;
     const double pf = pref[t * L + e];
     const int ngg = ng * (ng + 1) / 2, ngs = ng * ns;
-    for (int i = 0; i < nA; i++) {
-        int p;
-        if (t == 0) { if (i > j) continue; p = i * ng - i * (i - 1) / 2 + (j - i); }
-        else if (t == 1) p = ngg + i * ns + j;
-        else { if (i > j) continue; p = ngg + ngs + i * ns - i * (i - 1) / 2 + (j - i); }
-        double out = pf * ((double)Zh[i] + (double)Zl[i]);
-        if (rq.status) out = nan("");
-        rq.cl[(size_t)p * rq.n_sel + col] = out;
+#pragma unroll
+    for (int i = 0; i < kNB; i++) {
+#pragma unroll
+        for (int j = 0; j < kNB; j++) {
+            if (i >= nA || j >= nB) continue;
+            int p;
+            if (t == 0) { if (i > j) continue; p = i * ng - i * (i - 1) / 2 + (j - i); }
+            else if (t == 1) p = ngg + i * ns + j;
+            else { if (i > j) continue; p = ngg + ngs + i * ns - i * (i - 1) / 2 + (j - i); }
+            double out = pf * ((double)Zh[i][j] + (double)Zl[i][j]);
+            if (rq->status) out = nan("");
+            rq->cl[(size_t)p * rq->n_sel + col] = out;
+        }
     }
 }
 
@@ -718,8 +783,8 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
     const int Bpad = (n + kM - 1) / kM * kM;
     const float *UT = reinterpret_cast<const float *>(p->ws.tc.as<uint16_t>() + (size_t)kS * Bpad * p->Kp) + Bpad;
     const float *UTl = UT + (size_t)(p->max_clust + p->max_lens) * p->X * Bpad;
-    dim3 grid((n + 127) / 128, n_esel * p->max_tr, 3);
-    k_reduce_tc<<<grid, 128, 0, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel, n_esel,
+    dim3 grid((n + 31) / 32, n_esel, 3);
+    k_reduce_tc<<<grid, 32 * kRedChunks, 0, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel, n_esel,
                                      p->Rn / kQT, p->max_tr, p->d_pref);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;

@@ -342,11 +342,29 @@ extern "C" size_t blast_request_footprint(const blast_plan *p, const blast_reque
 // Stage requests, build device descriptors, and run fit + weights.  Shared by
 // the CUDA-core and tensor-core paths.  On success *d_esel / *n_esel hold the
 // union of the requests' ell selections.
+// Device address through which kernels may read or write host memory in place,
+// or nullptr: pinned mapped memory, or (when the GPU uses the host's page
+// tables, pageable != 0) any host address.
+static const void *device_view(const void *hp, int pageable)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, hp) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) return at.devicePointer;
+    if (at.type == cudaMemoryTypeUnregistered && pageable) return hp;
+    return nullptr;
+}
+
 int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, double *const *outs,
                 int out_mem_space, cudaStream_t s, ReqDev **dreq_out, int **d_esel, int *n_esel,
-                std::vector<ReqDev> &hreq)
+                std::vector<ReqDev> &hreq, std::vector<char> &direct_out)
 {
     Workspace &ws = p->ws;
+    int pageable = 0;
+    cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccessUsesHostPageTables, p->device);
+    direct_out.assign(n, 0);
     const int ntr_max = p->max_clust + p->max_lens;
     // ell union
     std::vector<int> esel;
@@ -384,9 +402,21 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
         memset(&h, 0, sizeof h);
         const int ntr = r.n_clust + r.n_lens;
         h.n_clust = r.n_clust; h.n_lens = r.n_lens; h.n_ptab = r.n_ptab; h.status = 0;
+        const double *hv[6] = {r.kern_chi, r.kern_Rchi, r.growth_chi, r.growth_Rchi, r.k_tab, r.p_tab};
+        const double *dv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        // in-place reads only when the call waits for the stream before it
+        // returns (host outputs), so host inputs are still read only during the call
+        bool direct = (r.mem_space == 0 && out_mem_space == 0);
+        for (int k = 0; direct && k < 6; k++) direct = (dv[k] = (const double *)device_view(hv[k], pageable)) != nullptr;
         if (r.mem_space == 1) {
             h.kern_chi = r.kern_chi; h.kern_Rchi = r.kern_Rchi; h.growth_chi = r.growth_chi;
             h.growth_Rchi = r.growth_Rchi; h.k_tab = r.k_tab; h.p_tab = r.p_tab;
+        } else if (direct) {
+            // host arrays the device can read in place (pinned and mapped, or any
+            // host memory on a system whose GPU uses the host page tables): the
+            // kernels stream them over the host link, no staging copies
+            h.kern_chi = dv[0]; h.kern_Rchi = dv[1]; h.growth_chi = dv[2];
+            h.growth_Rchi = dv[3]; h.k_tab = dv[4]; h.p_tab = dv[5];
         } else {
             double *base = ws.in.as<double>() + in_per * i;
             double *kc = base, *kR = kc + (size_t)ntr * p->X, *gc = kR + (size_t)ntr * p->Q;
@@ -413,6 +443,10 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
             if (ell_selected(&r, e)) h.e_out[e] = col++;
         h.n_sel = col;
         h.cl = (out_mem_space == 1) ? outs[i] : ws.cl.as<double>() + cl_per * i;
+        if (out_mem_space == 0) {  // a device-writable host output is written in place
+            double *o = (double *)device_view(outs[i], pageable);
+            if (o) { h.cl = o; direct_out[i] = 1; }
+        }
         const void *ptrs[] = {h.a64, h.a32, h.U64, h.V64, h.U32, h.V32, h.cl, h.kern_chi, h.kern_Rchi,
                               h.growth_chi, h.growth_Rchi, h.k_tab, h.p_tab};
         for (const void *q : ptrs)
@@ -429,11 +463,12 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
     return BLAST_OK;
 }
 
-int finish_batch(blast_plan *p, int n, const std::vector<ReqDev> &hreq, double *const *outs, int out_mem_space,
-                 cudaStream_t s)
+int finish_batch(blast_plan *p, int n, const std::vector<ReqDev> &hreq, const std::vector<char> &direct_out,
+                 double *const *outs, int out_mem_space, cudaStream_t s)
 {
     if (out_mem_space == 1) return BLAST_OK;
     for (int i = 0; i < n; i++) {
+        if (direct_out[i]) continue;  // written in place by the kernel
         size_t bytes = sizeof(double) * blast_npairs(hreq[i].n_clust, hreq[i].n_lens) * hreq[i].n_sel;
         BL_CUDA(cudaMemcpyAsync(outs[i], hreq[i].cl, bytes, cudaMemcpyDeviceToHost, s));
     }
@@ -466,7 +501,8 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
     ReqDev *dreq = nullptr;
     int *d_esel = nullptr, n_esel = 0;
     std::vector<ReqDev> hreq;
-    int rc = stage_batch(p, n, reqs, prec, outs, out_mem_space, s, &dreq, &d_esel, &n_esel, hreq);
+    std::vector<char> direct_out;
+    int rc = stage_batch(p, n, reqs, prec, outs, out_mem_space, s, &dreq, &d_esel, &n_esel, hreq, direct_out);
     if (rc) return rc;
     if (use_tc) {
         const size_t ybytes = (size_t)n * 3 * n_esel * p->X * (p->Rn / 32) * 2 * p->max_tr * 4;
@@ -491,7 +527,7 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
              })))
             return rc;
     }
-    rc = finish_batch(p, n, hreq, outs, out_mem_space, s);
+    rc = finish_batch(p, n, hreq, direct_out, outs, out_mem_space, s);
     if (!rc && out_mem_space == 0 && *p->h_err) {
         *p->h_err = 0;
         return BLAST_ETIMEOUT;
