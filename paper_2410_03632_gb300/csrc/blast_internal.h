@@ -67,8 +67,8 @@ struct blast_plan {
     // basis tables
     double *T64 = nullptr;          // [3][L][N][Q]
     float *T32 = nullptr;           // [3][L][N][Q]
-    uint16_t *Tsl = nullptr;        // [S][3 L Q][Kp] bf16 integer slices, K-major (n fastest)
-    float *scT = nullptr;           // [3 L Q] 2^(eT - 16 - 8(S-1)) per column
+    uint16_t *Tsl = nullptr;        // [S][3 L Q][Kp] bf16 slices (integer x 2^-8p), K-major (n fastest)
+    float *scT = nullptr;           // [3 L Q] 2^(eT - 16) per column
     int Kp = 0;                     // N rounded up to a multiple of 64 (zero padded)
     bool have64 = false, have32 = false, havebf = false;
     int *d_err = nullptr;           // host-mapped error word written by bounded device waits

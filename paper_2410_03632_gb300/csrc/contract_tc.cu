@@ -13,24 +13,28 @@
 //   a_b[n]     = 2^ea(b)    sum_p 2^(-8(p+1)) A_p[b][n],   A_p integers, |A_p| <= 256
 //   T~[.][n][q] = 2^eT(col) sum_p 2^(-8(p+1)) T_p[col][n]
 //
-// Every slice value is an integer held exactly in BF16, every product is
-// exact, and each level D_k = sum_{p+q=k} sum_n A_p T_q stays below 2^24, so
-// the FP32 tensor-core accumulation is exact.  The 15 slice pairs p+q <= 4
-// feed 5 level accumulators in TMEM; the epilogue combines the levels exactly
-// in 64-bit integers, W = sum_k D_k 2^(8(4-k)), turns W into an exact pair of
-// floats and scales by 2^(ea + eT - 48).  The R sum that follows also cancels
-// (w oscillates around R = 1), so it runs on unevaluated pairs: exact
-// products (FMA) and two-sum accumulation; the pairs reach the chi sum intact.
+// Slice p is stored as A_p 2^(-8p) (T_q 2^(-8q)): an integer of at most 9
+// bits times a power of two, exact in BF16.  Every product is exact, and level
+// k, D_k 2^(-8k) = sum_{p+q=k} sum_n (A_p 2^-8p)(T_q 2^-8q), is a multiple of
+// 2^(-8k) below 2^(23-8k) in magnitude, so the FP32 tensor-core accumulation
+// is exact.  The 15 slice pairs p+q <= 4 feed 5 level accumulators in TMEM;
+// the epilogue adds the levels with a cascade of fast two-sums, each exact for
+// operands on these grids, W 2^-32 = m + (e1 + e2 + e3 + e4), and scales by
+// 2^(ea + eT - 16).  The R sum that follows also cancels (w oscillates around
+// R = 1), so it runs on unevaluated pairs: exact products (FMA) and two-sum
+// accumulation, two columns at a time in packed FP32 pairs; the pairs reach
+// the chi sum intact.
 //
 // Warp roles (576 threads): warp 0 issues TMA loads of the basis slices,
 // warp 1 owns TMEM and issues tcgen05.mma (A = coefficient slices resident in
 // TMEM, B = basis slices in shared memory), warps 2..17 run the epilogue (one
-// TMEM lane = one cosmology per thread, four warps per lane quadrant).  Every
-// mbarrier wait is bounded; on timeout the kernel records an error code in
-// host-mapped memory and exits.
+// TMEM lane = one cosmology per thread, four warps per lane quadrant, joined
+// by a named barrier per quadrant).  Every mbarrier wait is bounded; on
+// timeout the kernel records an error code in host-mapped memory and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -42,7 +46,7 @@ constexpr int kS = BLAST_TC_SLICES;       // slices per operand
 constexpr int kQT = 32;                   // chi-R nodes per tile (MMA N)
 constexpr int kM = 128;                   // cosmologies per tile (MMA M)
 constexpr int kKC = 64;                   // K elements per 128-byte swizzle row
-constexpr int kStages = 6;
+constexpr int kStages = 4;
 constexpr int kEP = 4;                    // epilogue warps per TMEM lane quadrant
 constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 16 epilogue warps
 constexpr int kHC = 32 / kEP;             // columns per epilogue thread
@@ -51,7 +55,9 @@ constexpr uint32_t kACol = 2 * kS * kQT;          // TMEM column of the coeffici
 constexpr uint32_t kBSliceBytes = kQT * 128;      // 32 rows x 64 bf16
 constexpr uint32_t kBStageBytes = kS * kBSliceBytes;
 constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kCtrlBytes = 256;               // mbarriers, TMEM address, abort flag
 constexpr long long kWaitLimit = 4000000000LL;  // clock cycles (about 2 s)
+constexpr uint32_t kSuspendNs = 1000000;        // longest suspension of one phase test
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -75,26 +81,43 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// One test of a phase; a thread that finds it incomplete is suspended until the
+// phase completes or about kSuspendNs nanoseconds pass, so waiting warps do not
+// take issue slots from working ones.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
 
-// Bounded wait on a phase: false if it did not complete within kWaitLimit cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Barrier among n threads (whole warps) of the CTA on hardware barrier id (1..15).
+__device__ __forceinline__ void named_bar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Bounded wait on a phase: false if it did not complete within kWaitLimit
+// cycles.  With sleep_ns > 0 the thread sleeps between tests, doubling up to
+// 1 us: for the TMA and MMA warps, which wait most of the time and need not
+// answer within a few cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned sleep_ns = 0)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
+    while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > kWaitLimit) return false;
+        if (sleep_ns) {
+            __nanosleep(sleep_ns);
+            sleep_ns = min(2u * sleep_ns, 1024u);
+        }
+    }
     return true;
 }
 
@@ -134,6 +157,14 @@ __device__ __forceinline__ void umma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64
         ::"r"(d_tmem), "r"(a_tmem), "l"(bd), "r"(kIdesc), "r"(acc));
 }
 
+// True in exactly one lane of the (converged) warp.
+__device__ __forceinline__ bool elect_one()
+{
+    uint32_t p;
+    asm volatile("{\n\t.reg .pred P;\n\telect.sync _|P, 0xffffffff;\n\tselp.u32 %0, 1, 0, P;\n\t}\n" : "=r"(p));
+    return p != 0;
+}
+
 // Thirty-two consecutive 32-bit columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
 {
@@ -156,12 +187,10 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
-// Four consecutive 32-bit columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4])
+// Two consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&r)[2])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
 }
 
 // Knuth's two-sum: s + e == a + b exactly, s = fl(a + b).
@@ -173,48 +202,100 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     s = ss;
 }
 
-// Fast two-sum (|a| >= |b| or a == 0): s + e == a + b exactly.
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+// Packed pairs of FP32: lane x in the low and lane y in the high half of one
+// 64-bit register pair, one instruction for both lanes, rounded to nearest
+// like the scalar forms.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float x, float y)
 {
-    const float ss = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(ss, a));
+    f32x2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(x), "f"(y));
+    return d;
+}
+
+__device__ __forceinline__ float2 unpk2(f32x2 a)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Both lanes negated (sign bits flipped, exact).
+__device__ __forceinline__ f32x2 neg2(f32x2 a) { return a ^ 0x8000000080000000ull; }
+
+// Fast two-sum on both lanes: s + e == a + b exactly when |a| >= |b|, or when
+// a + b is representable.
+__device__ __forceinline__ void fast_two_sum2(f32x2 a, f32x2 b, f32x2 &s, f32x2 &e)
+{
+    s = add2(a, b);
+    e = sub2(b, sub2(s, a));
+}
+
+// Two-sum on both lanes: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum2(f32x2 a, f32x2 b, f32x2 &s, f32x2 &e)
+{
+    const f32x2 ss = add2(a, b);
+    const f32x2 bb = sub2(ss, a);
+    e = add2(sub2(a, sub2(ss, bb)), sub2(b, bb));
     s = ss;
 }
 
-// Exact float of an integer x < 2^23: x placed in the mantissa of 2^23, minus 2^23.
-__device__ __forceinline__ float u23_to_float(unsigned x)
+// Wait for this thread's TMEM loads; the registers they fill are operands, so
+// no use of them can move above the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[BLAST_TC_SLICES][2])
 {
-    return __fsub_rn(__uint_as_float(0x4B000000u | x), 8388608.0f);
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[1][0]), "+r"(r[1][1]), "+r"(r[2][0]), "+r"(r[2][1]),
+                   "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[4][0]), "+r"(r[4][1])
+                 :
+                 : "memory");
 }
-
-// x < 2^56 as h + l (h = x rounded to float, l the exact remainder as a float):
-// x = c2 2^46 + c1 2^23 + c0 with 23-bit pieces, each exact, summed by fast two-sums.
-__device__ __forceinline__ void split_u56(unsigned long long x, float &h, float &l)
-{
-    const float f0 = u23_to_float((unsigned)(x & 0x7FFFFFull));
-    const float f1 = __fmul_rn(u23_to_float((unsigned)((x >> 23) & 0x7FFFFFull)), 8388608.0f);
-    const float f2 = __fmul_rn(u23_to_float((unsigned)(x >> 46)), 70368744177664.0f);  // 2^46
-    float s1, e1, s2, e2;
-    fast_two_sum(f2, f1, s1, e1);
-    fast_two_sum(s1, f0, s2, e2);
-    h = s2;
-    l = __fadd_rn(e1, e2);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // ---------------------------------------------------------------- slicing
-// x (|x| < 2^e) -> S integers in [-256, 256], each exact in BF16.
-__device__ __forceinline__ void slice8(double xn, uint16_t (&out)[kS])
+// x (|x| < 1) -> S slices: integers in [-256, 256] times 2^(-8p) f for slice
+// p, f a power of two (2^-126 <= 2^(-8p) f <= 1), each exact in BF16: the
+// powers of two only move the exponent.
+__device__ __forceinline__ void slice8(double xn, uint16_t (&out)[kS], float f = 1.0f)
 {
     double r = xn * 256.0;
+    float sc = f;
 #pragma unroll
     for (int p = 0; p < kS; p++) {
         double q = rint(r);
-        out[p] = __bfloat16_as_ushort(__float2bfloat16_rn((float)q));
+        out[p] = __bfloat16_as_ushort(__float2bfloat16_rn(__fmul_rn((float)q, sc)));
         r = (r - q) * 256.0;
+        sc *= 0.00390625f;
     }
 }
 
@@ -231,10 +312,9 @@ __global__ void k_coef_slices(const ReqDev *__restrict__ reqs, int n, int N, int
     for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
-    const double inv = ldexp(1.0, -e);
     for (int k = lane; k < Kp; k += 32) {
         uint16_t s[kS];
-        slice8((a && k < N) ? a[k] * inv : 0.0, s);
+        slice8((a && k < N) ? ldexp(a[k], -e) : 0.0, s);
 #pragma unroll
         for (int p = 0; p < kS; p++) A[((size_t)p * Bpad + b) * Kp + k] = s[p];
     }
@@ -249,26 +329,38 @@ __global__ void k_coef_slices(const ReqDev *__restrict__ reqs, int n, int N, int
     }
 }
 
-// Basis slices, one thread per column (t, l, q): T_p[col][n] and 2^(eT - 16 - 8(S-1)).
+// Basis slices, one warp per tile of kQT columns (t, l, q0..q0+31), a lane per
+// column: T_p[col][n] 2^(-8p) 2^(eT(col) - eG) with eG the largest column
+// exponent of the tile, and one scale 2^(eG - 16) per tile.  A column keeps
+// its own 40-bit fixed-point precision; the power of two moves the exponent
+// only.  Columns more than 2^90 below the tile's largest (or in tiles whose
+// scale underflows FP32) are zero: they could not change the tile's sum.
 __global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q, int Kp, uint16_t *Tsl, float *scT)
 {
     const size_t ncol = (size_t)3 * L * Q;
-    for (size_t col = (size_t)blockIdx.x * blockDim.x + threadIdx.x; col < ncol;
-         col += (size_t)gridDim.x * blockDim.x) {
+    const size_t ntile = ncol / kQT;
+    const int lane = threadIdx.x & 31;
+    for (size_t tile = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; tile < ntile;
+         tile += ((size_t)gridDim.x * blockDim.x) / 32) {
+        const size_t col = tile * kQT + lane;
         const size_t tl = col / Q, q = col % Q;
         const double *src = T + tl * (size_t)N * Q + q;
         double mx = 0.0;
         for (int k = 0; k < N; k++) mx = fmax(mx, fabs(src[(size_t)k * Q]));
         int e = 0;
         if (mx > 0.0) frexp(mx, &e);
-        const double inv = ldexp(1.0, -e);
+        int eG = (mx > 0.0) ? e : INT_MIN;
+        for (int o = 16; o; o >>= 1) eG = max(eG, __shfl_xor_sync(0xffffffffu, eG, o));
+        const float scf = (eG != INT_MIN) ? (float)ldexp(1.0, eG - 16) : 0.0f;
+        const bool keep = mx > 0.0 && scf != 0.0f && e - eG >= -90;
+        const float shift = keep ? ldexpf(1.0f, e - eG) : 0.0f;
         for (int k = 0; k < Kp; k++) {
             uint16_t s[kS];
-            slice8(k < N ? src[(size_t)k * Q] * inv : 0.0, s);
+            slice8((k < N && keep) ? ldexp(src[(size_t)k * Q], -e) : 0.0, s, shift);
 #pragma unroll
             for (int p = 0; p < kS; p++) Tsl[((size_t)p * ncol + col) * Kp + k] = s[p];
         }
-        scT[col] = (mx > 0.0) ? (float)ldexp(1.0, e - 16 - 8 * (kS - 1)) : 0.0f;
+        if (lane == 0) scT[tile] = scf;
     }
 }
 
@@ -277,7 +369,7 @@ struct TcArgs {
     const ReqDev *reqs;
     int n, Bpad, nbt, nqt, n_esel, L, Q, Rn, RT, MT;
     const int *esel;
-    const float *scT;    // [3][L][Q]
+    const float *scT;    // [3][L][Q / kQT] one scale per tile
     const float *sa;     // [Bpad]
     const uint16_t *A;   // [S][Bpad][64] coefficient slices
     float *Y;            // [3][n_esel][X][RT][MT][n]  (cosmology fastest)
@@ -291,12 +383,13 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     // 1024-byte alignment for the swizzled tiles
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sB = smem;                                  // kStages x kS x 4 KB
-    uint64_t *bars = (uint64_t *)(sB + kStages * kBStageBytes);
+    uint64_t *bars = (uint64_t *)(sB + kStages * kBStageBytes);  // kCtrlBytes of control words
     uint64_t *full = bars, *empty = bars + kStages, *aready = bars + 2 * kStages;
-    uint64_t *tfull = aready + 1, *tempty = tfull + 2, *yfull = tempty + 2, *yempty = yfull + 2;
-    float *ybuf = (float *)(yempty + 2);                      // [2][kEP-1][kM][2 kNB] partial pairs
-    uint32_t *tmem_slot = (uint32_t *)(ybuf + 2 * (kEP - 1) * kM * 2 * kNB);
+    uint64_t *tfull = aready + 1, *tempty = tfull + 2;
+    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    float *ybuf = (float *)((unsigned char *)bars + kCtrlBytes);   // [2][kEP-1][2 kNB][kM] partial pairs
+    f32x2 *vsm = (f32x2 *)(ybuf + 2 * (kEP - 1) * 2 * kNB * kM);   // [kNB][kHC/2][128 kEP] weights
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int btile = blockIdx.x % args.nbt;
@@ -307,7 +400,6 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         mbar_init(aready, 128);
         for (int i = 0; i < 2; i++) {
             mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128 * kEP);
-            mbar_init(&yfull[i], 128 * (kEP - 1)); mbar_init(&yempty[i], 128);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -323,7 +415,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ------------------------------------------------ TMA producer (whole warp waits, lane 0 issues)
+        // ------------------------------------------------ TMA producer (whole warp waits, one lane issues)
         uint32_t g = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < args.nbt * args.nqt; u += gridDim.x) {
@@ -331,12 +423,13 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
             for (int it = 0; it < n_iter_unit; it++, g++) {
                 const int st = g % kStages;
                 const uint32_t ph = (g / kStages) & 1;
-                if (*abort_flag || !mbar_wait(&empty[st], ph ^ 1)) {
+                const bool bad = *abort_flag || !mbar_wait(&empty[st], ph ^ 1, 64);
+                if (__any_sync(0xffffffffu, bad)) {
                     if (lane == 0) { atomicExch(args.err, 1); *abort_flag = 1; }
                     ok = false;
                     break;
                 }
-                if (lane == 0) {
+                if (elect_one()) {
                     const int t = it / args.n_esel, e = args.esel[it % args.n_esel];
                     const int row = (t * args.L + e) * args.Q + q0;
                     mbar_expect_tx(&full[st], kBStageBytes);
@@ -347,14 +440,16 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         }
         // drain: every issued load has landed before the CTA may exit
         for (uint32_t h = (g > kStages ? g - kStages : 0); h < g; h++)
-            mbar_wait(&full[h % kStages], (h / kStages) & 1);
+            mbar_wait(&full[h % kStages], (h / kStages) & 1, 64);
         __syncwarp();
     } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer (whole warp waits, lane 0 issues)
-        bool ok = mbar_wait(aready, 0);  // coefficient slices written into TMEM by the epilogue
+        // ------------------------------------------------ MMA issuer (whole warp waits; each MMA is
+        // issued by one elected lane of the converged warp)
+        bool ok = __all_sync(0xffffffffu, mbar_wait(aready, 0, 64));  // coefficient slices in TMEM
         if (!ok && lane == 0) { atomicExch(args.err, 2); *abort_flag = 1; }
         tc_fence_after();
-        const uint32_t b0 = smem_u32(sB);
+        const uint32_t b0 = __shfl_sync(0xffffffffu, smem_u32(sB), 0);  // warp-uniform operands
+        const uint32_t tm = __shfl_sync(0xffffffffu, tmem, 0);
         uint32_t g = 0;
         for (int u = blockIdx.x; ok && u < args.nbt * args.nqt; u += gridDim.x) {
             for (int it = 0; it < n_iter_unit; it++, g++) {
@@ -362,28 +457,32 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                 const uint32_t ph = (g / kStages) & 1;
                 const int buf = g & 1;
                 const uint32_t tph = (g >> 1) & 1;
-                if (*abort_flag || !mbar_wait(&full[st], ph) || !mbar_wait(&tempty[buf], tph ^ 1)) {
+                const bool bad = *abort_flag || !mbar_wait(&full[st], ph, 64) || !mbar_wait(&tempty[buf], tph ^ 1, 64);
+                if (__any_sync(0xffffffffu, bad)) {
                     if (lane == 0) { atomicExch(args.err, 3); *abort_flag = 1; }
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                if (lane == 0) {
-                    const uint32_t dbase = tmem + buf * (kS * kQT);
-                    const uint32_t bst = b0 + st * kBStageBytes;
+                // operands of the 60 MMAs: accumulator levels of this buffer, coefficient
+                // slices in TMEM, basis slice descriptors offset from this stage's first
+                const uint32_t dbase = tm + buf * (kS * kQT);
+                const uint64_t bbase = sdesc(b0 + st * kBStageBytes);
+                if (elect_one()) {
 #pragma unroll
                     for (int lev = 0; lev < kS; lev++) {
 #pragma unroll
                         for (int p = 0; p <= lev; p++) {
                             const int q = lev - p;
 #pragma unroll
-                            for (int kk = 0; kk < kKC / 16; kk++) {
-                                const uint32_t at = tmem + kACol + p * (kKC / 2) + kk * 8;
-                                const uint64_t bd = sdesc(bst + q * kBSliceBytes + kk * 32);
-                                umma_ts(dbase + lev * kQT, at, bd, (p > 0 || kk > 0) ? 1u : 0u);
-                            }
+                            for (int kk = 0; kk < kKC / 16; kk++)
+                                umma_ts(dbase + lev * kQT, tm + kACol + p * (kKC / 2) + kk * 8,
+                                        bbase + (uint64_t)((q * kBSliceBytes + kk * 32) >> 4), (p > 0 || kk > 0) ? 1u : 0u);
                         }
                     }
+                }
+                __syncwarp();
+                if (elect_one()) {
                     umma_commit(&empty[st]);
                     umma_commit(&tfull[buf]);
                 }
@@ -421,13 +520,19 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
             tc_fence_before();
             mbar_arrive(aready);
         }
+        // Every thread of the quadrant's four warps passes the same number of
+        // named barriers; after a wait runs out the warps skip the work but keep
+        // the count, so no barrier is left waiting.
+        const int bar_id = 1 + quad;
         uint32_t g = 0;
-        bool ok = true;
-        for (int u = blockIdx.x; ok && u < args.nbt * args.nqt; u += gridDim.x) {
+        bool dead = false;
+        for (int u = blockIdx.x; u < args.nbt * args.nqt; u += gridDim.x) {
             const int q0 = (u / args.nbt) * kQT;
             const int a = q0 / args.Rn, rt = (q0 % args.Rn) / kQT;
-            float wv[kNB][kHC];  // quadrature weights of this cosmology, times its scale 2^ea
-            for (int t = 0; t < 3 && ok; t++) {
+            // quadrature weights of this cosmology times its scale 2^ea, kept in this
+            // thread's own slots of shared memory (read back only by this thread)
+            f32x2 *vme = vsm + (threadIdx.x - 64);
+            for (int t = 0; t < 3; t++) {
                 const int offB = (t == 0) ? 0 : ng, nB = (t == 0) ? ng : ns;
                 if (t < 2) {
 #pragma unroll
@@ -438,93 +543,113 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                                 : nullptr;
 #pragma unroll
                         for (int c = 0; c < kHC / 4; c++) {
-                            float4 v = src ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-                            wv[j][4 * c] = v.x * sa; wv[j][4 * c + 1] = v.y * sa;
-                            wv[j][4 * c + 2] = v.z * sa; wv[j][4 * c + 3] = v.w * sa;
+                            const float4 v = src ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            vme[(j * (kHC / 2) + 2 * c) * (128 * kEP)] = pk2(v.x * sa, v.y * sa);
+                            vme[(j * (kHC / 2) + 2 * c + 1) * (128 * kEP)] = pk2(v.z * sa, v.w * sa);
                         }
                     }
                 }
                 for (int es = 0; es < args.n_esel; es++, g++) {
                     const int buf = g & 1;
                     const uint32_t tph = (g >> 1) & 1;
-                    if (!mbar_wait(&tfull[buf], tph)) { atomicExch(args.err, 4); ok = false; break; }
-                    tc_fence_after();
-                    const int e = args.esel[es];
-                    const float *sc = args.scT + ((size_t)t * args.L + e) * args.Q + q0 + cb;
-                    // R-sum of this thread's columns as an unevaluated pair (Sh + Sl): each
-                    // product V w is split exactly (FMA) and each addition's rounding error
-                    // is kept (two-sum), so the sum survives the cancellation of oscillating w
+                    if (!dead) {
+                        bool lost = *abort_flag != 0;
+                        if (!lost && !mbar_wait(&tfull[buf], tph)) {
+                            lost = true;
+                            atomicExch(args.err, 4);
+                            *abort_flag = 1;
+                        }
+                        dead = __any_sync(0xffffffffu, lost);
+                    }
                     float Sh[kNB], Sl[kNB];
 #pragma unroll
                     for (int j = 0; j < kNB; j++) { Sh[j] = 0.f; Sl[j] = 0.f; }
+                    if (!dead) {
+                        tc_fence_after();
+                        const uint32_t tcol = tmem + lane_addr + buf * (kS * kQT) + cb;
+                        // R-sum of this thread's columns, two columns per packed lane pair, as
+                        // negated unevaluated sums An + Bn: each product V w is split exactly
+                        // (FMA) and each addition's rounding error is kept (two-sum), so the
+                        // sum survives the cancellation of oscillating w
+                        f32x2 An[kNB], Bn[kNB];
 #pragma unroll
-                    for (int c0 = 0; c0 < kHC; c0 += 4) {
-                        uint32_t D[kS][4];
+                        for (int j = 0; j < kNB; j++) { An[j] = 0ull; Bn[j] = 0ull; }
+                        // levels of the next column pair load while this pair is summed
+                        uint32_t D[kS][2];
 #pragma unroll
-                        for (int lev = 0; lev < kS; lev++)
-                            tmem_ld4(tmem + lane_addr + buf * (kS * kQT) + lev * kQT + cb + c0, D[lev]);
-                        const float4 s4 = __ldg(reinterpret_cast<const float4 *>(sc + c0));
-                        const float scv[4] = {s4.x, s4.y, s4.z, s4.w};
-                        tmem_wait_ld();
-                        if (c0 + 4 == kHC) {  // every level of this buffer is in registers: release it
-                            tc_fence_before();
-                            mbar_arrive(&tempty[buf]);
-                        }
+                        for (int lev = 0; lev < kS; lev++) tmem_ld2(tcol + lev * kQT, D[lev]);
 #pragma unroll
-                        for (int c = 0; c < 4; c++) {
-                            // exact: W = sum_k D_k 2^(8(4-k)) with |D_0| <= 2^22, |D_k| < 2^23 (K <= 64),
-                            // so both 32-bit partial words fit without overflow
-                            const int d0 = __float2int_rn(__uint_as_float(D[0][c]));
-                            const int d1 = __float2int_rn(__uint_as_float(D[1][c]));
-                            const int d2 = __float2int_rn(__uint_as_float(D[2][c]));
-                            const int d3 = __float2int_rn(__uint_as_float(D[3][c]));
-                            const int d4 = __float2int_rn(__uint_as_float(D[4][c]));
-                            const int hi = d0 * 256 + d1, mid = d2 * 256 + d3;
-                            const long long W = ((long long)hi << 24) + ((long long)mid << 8) + d4;
-                            // |W| < 2^56 as an exact pair wh + wl of floats, from three 23-bit pieces
-                            // converted exactly without conversion instructions (a 64-bit
-                            // conversion would run on the FP64 pipe)
-                            const unsigned long long Aw = (unsigned long long)(W < 0 ? -W : W);
-                            float wh, wl;
-                            split_u56(Aw, wh, wl);
-                            const float sgn = (W < 0) ? -scv[c] : scv[c];
-                            wh = __fmul_rn(wh, sgn);
-                            wl = __fmul_rn(wl, sgn);
+                        for (int cp = 0; cp < kHC / 2; cp++) {
+                            tmem_wait_ld(D);
+                            f32x2 d[kS];
+#pragma unroll
+                            for (int lev = 0; lev < kS; lev++) d[lev] = pk2(__uint_as_float(D[lev][0]), __uint_as_float(D[lev][1]));
+                            if (cp + 1 < kHC / 2) {
+#pragma unroll
+                                for (int lev = 0; lev < kS; lev++) tmem_ld2(tcol + lev * kQT + 2 * (cp + 1), D[lev]);
+                            } else {  // every level of this buffer is in registers: release it
+                                tc_fence_before();
+                                mbar_arrive(&tempty[buf]);
+                            }
+                            // Level k holds D_k 2^(-8k) 2^(eT - eG), an integer multiple of
+                            // 2^(-8k) 2^(eT - eG) below 2^(23-8k) 2^(eT - eG) in magnitude, so
+                            // every fast two-sum of the cascade is exact:
+                            // W 2^(eT - eG - 32) = m + (e1 + e2 + e3 + e4), one rounding in the
+                            // low part only
+                            f32x2 m, e1, e2, e3, e4;
+                            fast_two_sum2(d[0], d[1], m, e1);
+                            fast_two_sum2(m, d[2], m, e2);
+                            fast_two_sum2(m, d[3], m, e3);
+                            fast_two_sum2(m, d[4], m, e4);
+                            const f32x2 lo = add2(add2(e1, e2), add2(e3, e4));
+                            const f32x2 mn = neg2(m);
 #pragma unroll
                             for (int j = 0; j < kNB; j++) {
-                                const float v = wv[j][c0 + c];
-                                const float pr = __fmul_rn(v, wh);
-                                const float pe = fmaf(v, wl, fmaf(v, wh, -pr));
-                                float se;
-                                two_sum(Sh[j], pr, Sh[j], se);
-                                Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, pe));
+                                const f32x2 v = vme[(j * (kHC / 2) + cp) * (128 * kEP)];
+                                const f32x2 prn = mul2(v, mn);                  // -fl(v m)
+                                const f32x2 pe = fma2(v, lo, fma2(v, m, prn));  // v lo + (v m - fl(v m))
+                                f32x2 se;
+                                two_sum2(An[j], prn, An[j], se);
+                                Bn[j] = add2(Bn[j], sub2(se, pe));
                             }
+                        }
+                        // both lanes into one pair per tracer: S = -(An.x + An.y) - (Bn.x + Bn.y)
+#pragma unroll
+                        for (int j = 0; j < kNB; j++) {
+                            const float2 A2 = unpk2(An[j]), B2 = unpk2(Bn[j]);
+                            float h, el;
+                            two_sum(A2.x, A2.y, h, el);
+                            Sh[j] = -h;
+                            Sl[j] = -__fadd_rn(el, __fadd_rn(B2.x, B2.y));
                         }
                     }
-                    // add the column parts: parts 1.. hand their pairs to part 0
-                    const int yb = g & 1;
-                    const uint32_t yph = (g >> 1) & 1;
+                    // add the column parts: parts 1.. hand their pairs to part 0 through
+                    // shared memory ([part - 1][2 kNB][kM], double buffered by iteration)
+                    float *yq = ybuf + (size_t)(g & 1) * (kEP - 1) * 2 * kNB * kM;
                     if (part > 0) {
-                        float *slot = ybuf + (((size_t)yb * (kEP - 1) + part - 1) * kM + bl_) * (2 * kNB);
-                        if (!mbar_wait(&yempty[yb], yph ^ 1)) { atomicExch(args.err, 5); ok = false; break; }
+                        float *slot = yq + (size_t)(part - 1) * 2 * kNB * kM + bl_;
 #pragma unroll
-                        for (int j = 0; j < kNB; j++) { slot[j] = Sh[j]; slot[kNB + j] = Sl[j]; }
-                        mbar_arrive(&yfull[yb]);
-                    } else {
-                        if (!mbar_wait(&yfull[yb], yph)) { atomicExch(args.err, 6); ok = false; break; }
+                        for (int j = 0; j < kNB; j++) { slot[j * kM] = Sh[j]; slot[(kNB + j) * kM] = Sl[j]; }
+                    }
+                    named_bar_sync(bar_id, 32 * kEP);
+                    if (part == 0 && !dead) {
 #pragma unroll
                         for (int q = 0; q < kEP - 1; q++) {
-                            const float *slot = ybuf + (((size_t)yb * (kEP - 1) + q) * kM + bl_) * (2 * kNB);
+                            const float *slot = yq + (size_t)q * 2 * kNB * kM + bl_;
 #pragma unroll
                             for (int j = 0; j < kNB; j++) {
                                 float se;
-                                two_sum(Sh[j], slot[j], Sh[j], se);
-                                Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, slot[kNB + j]));
+                                two_sum(Sh[j], slot[j * kM], Sh[j], se);
+                                Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, slot[(kNB + j) * kM]));
                             }
                         }
-                        mbar_arrive(&yempty[yb]);
                         if (valid) {
-                            // pair (hi, lo) of tracer j at j and MT + j
+                            // the tile's scale 2^(eG - 16) (exact), then the pair (hi, lo)
+                            // of tracer j at j and MT + j
+                            const float tsc =
+                                args.scT[((size_t)t * args.L + args.esel[es]) * (args.Q / kQT) + q0 / kQT];
+#pragma unroll
+                            for (int j = 0; j < kNB; j++) { Sh[j] *= tsc; Sl[j] *= tsc; }
                             float *y = args.Y +
                                        ((((size_t)t * args.n_esel + es) * (args.Q / args.Rn) + a) * args.RT + rt) *
                                            (size_t)(2 * args.MT) * args.n + b;
@@ -712,7 +837,11 @@ size_t tc_ws_bytes(const blast_plan *p, int Bpad)
            2 * (size_t)(p->max_clust + p->max_lens) * p->X * Bpad * 4 + 256;
 }
 
-size_t tc_smem_bytes() { return 1024 + kStages * kBStageBytes + 256 + 2 * (kEP - 1) * kM * 2 * kNB * 4; }
+size_t tc_smem_bytes()
+{
+    return 1024 + kStages * kBStageBytes + kCtrlBytes + 2 * (kEP - 1) * 2 * kNB * kM * sizeof(float) +
+           kNB * (kHC / 2) * 128 * kEP * sizeof(f32x2);
+}
 
 }  // namespace
 
