@@ -372,7 +372,7 @@ struct TcArgs {
     const float *scT;    // [3][L][Q / kQT] one scale per tile
     const float *sa;     // [Bpad]
     const uint16_t *A;   // [S][Bpad][64] coefficient slices
-    float *Y;            // [3][n_esel][X][RT][MT][n]  (cosmology fastest)
+    float *Y;            // [3][n_esel][X][n][RT][MT] pairs (hi, lo)
     int *err;            // host-mapped error word
 };
 
@@ -650,15 +650,14 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                                 args.scT[((size_t)t * args.L + args.esel[es]) * (args.Q / kQT) + q0 / kQT];
 #pragma unroll
                             for (int j = 0; j < kNB; j++) { Sh[j] *= tsc; Sl[j] *= tsc; }
-                            float *y = args.Y +
-                                       ((((size_t)t * args.n_esel + es) * (args.Q / args.Rn) + a) * args.RT + rt) *
-                                           (size_t)(2 * args.MT) * args.n + b;
+                            // Y[t][es][a][b][rt][j] pairs (hi, lo): one cosmology's R tiles of a
+                            // chi node are contiguous for the reduction's vector loads
+                            float2 *y = reinterpret_cast<float2 *>(args.Y) +
+                                        ((((size_t)t * args.n_esel + es) * (args.Q / args.Rn) + a) * args.n + b) *
+                                            (size_t)(args.RT * args.MT) + (size_t)rt * args.MT;
 #pragma unroll
                             for (int j = 0; j < kNB; j++)
-                                if (j < args.MT) {
-                                    y[(size_t)j * args.n] = Sh[j];
-                                    y[(size_t)(args.MT + j) * args.n] = Sl[j];
-                                }
+                                if (j < args.MT) y[j] = make_float2(Sh[j], Sl[j]);
                         }
                     }
                 }
@@ -674,18 +673,22 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
 }
 
 // Sum over R tiles and chi nodes for the tensor-core path, one thread per
-// (cosmology, type, ell) accumulating every tracer pair (i, j):
+// (cosmology, type, ell, chi chunk) accumulating every tracer pair (i, j):
 //   s_j(a) = sum_rt Y(t, l, a, rt, j)          (pairs (hi, lo), two-sum)
 //   C_ij(l) = N_AB(l) sum_a U_i(a) s_j(a)      (exact products, two-sum)
-constexpr int kRedChunks = 8;  // chi chunks per (cosmology, type, ell): one warp each
-constexpr int kRedRT = 2;      // R tiles whose loads are issued together
+// A block is 32 cosmologies x kRedChunks chi chunks (one warp each); the chunks
+// are added in a tree through shared memory.  The loads of the next group of
+// R tiles are in flight while the current group is summed.
+constexpr int kRedChunks = 16;  // chi chunks per (cosmology, type, ell): one warp each
+constexpr int kRedRT = 2;       // R tiles per load group
 
-__global__ void __launch_bounds__(32 * kRedChunks, 2)
+__global__ void __launch_bounds__(32 * kRedChunks, 1)
 k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const float *__restrict__ UT,
             const float *__restrict__ UTl, int n, int Bpad, int X, int L, const int *__restrict__ esel, int n_esel,
             int RT, int MT, const double *__restrict__ pref)
 {
-    __shared__ float red[kRedChunks / 2][32][2 * kNB * kNB];
+    extern __shared__ float red_raw[];  // [kRedChunks / 2][32][2 kNB kNB]
+    float(*red)[32][2 * kNB * kNB] = reinterpret_cast<float(*)[32][2 * kNB * kNB]>(red_raw);
     const int lane = threadIdx.x & 31, chunk = threadIdx.x >> 5;
     const int b = blockIdx.x * 32 + lane;
     const int es = blockIdx.y, t = blockIdx.z;
@@ -700,53 +703,75 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
     for (int i = 0; i < kNB; i++)
 #pragma unroll
         for (int j = 0; j < kNB; j++) { Zh[i][j] = 0.f; Zl[i][j] = 0.f; }
-    const size_t ystride = (size_t)n;  // between tracer slots
-    const float *Yp = Y + ((size_t)t * n_esel + es) * (size_t)X * RT * 2 * MT * n + b;
     const int per = (X + kRedChunks - 1) / kRedChunks;
     const int a0 = chunk * per, a1 = min(X, a0 + per);
-    for (int a = a0; active && a < a1; a++) {
-        float sh[kNB], sl[kNB];
+    const int ngrp = (RT + kRedRT - 1) / kRedRT;
+    const int total = active ? max(0, a1 - a0) * ngrp : 0;
+    // (hi, lo) of R tile rt, tracer j, at chi node a: Yb[(a n) RT MT + rt MT + j]
+    const float2 *Yb = reinterpret_cast<const float2 *>(Y) + ((size_t)t * n_esel + es) * (size_t)X * n * RT * MT +
+                       (size_t)b * RT * MT;
+    auto load_group = [&](int it, float2 (&v)[kRedRT][kNB]) {
+        const int a = a0 + it / ngrp, rt0 = (it % ngrp) * kRedRT;
+        const float2 *y = Yb + (size_t)a * n * RT * MT;
 #pragma unroll
-        for (int j = 0; j < kNB; j++) { sh[j] = 0.f; sl[j] = 0.f; }
-        // kRedRT R tiles per round, every load of the round issued before the sums
-        for (int rt0 = 0; rt0 < RT; rt0 += kRedRT) {
-            float v[kRedRT][2 * kNB];
+        for (int k = 0; k < kRedRT; k++)
 #pragma unroll
-            for (int k = 0; k < kRedRT; k++) {
-                const bool ok = rt0 + k < RT;
-                const float *yy = Yp + ((size_t)a * RT + rt0 + k) * 2 * MT * ystride;
+            for (int j = 0; j < kNB; j++)
+                v[k][j] = (rt0 + k < RT && j < nB) ? __ldg(y + (size_t)(rt0 + k) * MT + j) : make_float2(0.f, 0.f);
+    };
+    float2 cur[kRedRT][kNB];
+    if (total > 0) load_group(0, cur);
+    float sh[kNB], sl[kNB];
+#pragma unroll
+    for (int j = 0; j < kNB; j++) { sh[j] = 0.f; sl[j] = 0.f; }
+    float uh[kNB], ul[kNB];
+    for (int it = 0; it < total; it++) {
+        const int a = a0 + it / ngrp, g = it % ngrp;
+        if (g == 0) {  // chi weights of this node, in flight with the R tiles
+#pragma unroll
+            for (int i = 0; i < kNB; i++) {
+                const size_t ui = ((size_t)(offA + i) * X + a) * Bpad + b;
+                uh[i] = (i < nA) ? __ldg(UT + ui) : 0.f;
+                ul[i] = (i < nA) ? __ldg(UTl + ui) : 0.f;
+            }
+        }
+        float2 nxt[kRedRT][kNB];
+        if (it + 1 < total) load_group(it + 1, nxt);
+#pragma unroll
+        for (int k = 0; k < kRedRT; k++)
+#pragma unroll
+            for (int j = 0; j < kNB; j++) {
+                float se;
+                two_sum(sh[j], cur[k][j].x, sh[j], se);
+                sl[j] = __fadd_rn(sl[j], __fadd_rn(se, cur[k][j].y));
+            }
+        if (g == ngrp - 1) {
+            float sv[kNB], sle[kNB];
+#pragma unroll
+            for (int j = 0; j < kNB; j++) {
+                two_sum(sh[j], sl[j], sv[j], sle[j]);
+                sh[j] = 0.f;
+                sl[j] = 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < kNB; i++) {
+                if (i >= nA) continue;
 #pragma unroll
                 for (int j = 0; j < kNB; j++) {
-                    v[k][j] = (ok && j < nB) ? __ldg(yy + (size_t)j * ystride) : 0.f;
-                    v[k][kNB + j] = (ok && j < nB) ? __ldg(yy + (size_t)(MT + j) * ystride) : 0.f;
+                    if (j >= nB) continue;
+                    const float pr = __fmul_rn(uh[i], sv[j]);
+                    const float pe = fmaf(uh[i], sle[j], fmaf(ul[i], sv[j], fmaf(uh[i], sv[j], -pr)));
+                    float se;
+                    two_sum(Zh[i][j], pr, Zh[i][j], se);
+                    Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, pe));
                 }
             }
+        }
+        if (it + 1 < total) {
 #pragma unroll
             for (int k = 0; k < kRedRT; k++)
 #pragma unroll
-                for (int j = 0; j < kNB; j++) {
-                    float se;
-                    two_sum(sh[j], v[k][j], sh[j], se);
-                    sl[j] = __fadd_rn(sl[j], __fadd_rn(se, v[k][kNB + j]));
-                }
-        }
-        float sv[kNB], sle[kNB];
-#pragma unroll
-        for (int j = 0; j < kNB; j++) two_sum(sh[j], sl[j], sv[j], sle[j]);
-#pragma unroll
-        for (int i = 0; i < kNB; i++) {
-            if (i >= nA) continue;
-            const size_t ui = ((size_t)(offA + i) * X + a) * Bpad + b;
-            const float uh = UT[ui], ul = UTl[ui];
-#pragma unroll
-            for (int j = 0; j < kNB; j++) {
-                if (j >= nB) continue;
-                const float pr = __fmul_rn(uh, sv[j]);
-                const float pe = fmaf(uh, sle[j], fmaf(ul, sv[j], fmaf(uh, sv[j], -pr)));
-                float se;
-                two_sum(Zh[i][j], pr, Zh[i][j], se);
-                Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, pe));
-            }
+                for (int j = 0; j < kNB; j++) cur[k][j] = nxt[k][j];
         }
     }
     // tree over the chi chunks: the upper half of the warps hands its pairs down
@@ -913,7 +938,9 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
     const float *UT = reinterpret_cast<const float *>(p->ws.tc.as<uint16_t>() + (size_t)kS * Bpad * p->Kp) + Bpad;
     const float *UTl = UT + (size_t)(p->max_clust + p->max_lens) * p->X * Bpad;
     dim3 grid((n + 31) / 32, n_esel, 3);
-    k_reduce_tc<<<grid, 32 * kRedChunks, 0, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel, n_esel,
+    const int smem = kRedChunks / 2 * 32 * 2 * kNB * kNB * (int)sizeof(float);
+    BL_CUDA(cudaFuncSetAttribute(k_reduce_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_reduce_tc<<<grid, 32 * kRedChunks, smem, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel, n_esel,
                                      p->Rn / kQT, p->max_tr, p->d_pref);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
