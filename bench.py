@@ -319,6 +319,10 @@ def run_blast(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    serve = None
+    if args.serve_seconds > 0 and rank == 0:
+        serve = serve_latency(plan, rqs, prec_main, dtype_main, args.serve_rate, args.serve_seconds)
+
     launches = sum(prof_main[n][1] for n in bl.KERNEL_CLASS_NAMES)
     value = world * B * args.steps / (ms_main * 1e-3)
     line = {
@@ -332,8 +336,9 @@ def run_blast(args):
                  "dtype": "f64"},
         "err_vs_fp64": {"max_eij": err, "bound": 1e-4,
                         "def": "|C-C_fp64|/sqrt(C_ii C_jj), every cosmology of the batch, all pairs and ells"},
-        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                       "what": "one cosmology, FP32 path, device inputs"},
+        "latency_ms": serve,
+        "single_call_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                                   "what": "one blast_cl call, one cosmology, FP32 path, device inputs"},
         "roofline": roof,
         "e2e": {"value": world * B * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -353,6 +358,65 @@ def run_blast(args):
         dist.destroy_process_group()
 
 
+def serve_latency(plan, rqs, prec, prec_name, rate, seconds, seed=2000):
+    """Serving latency through blast_submit / blast_poll: seeded Poisson
+    arrivals at ``rate`` requests/s for ``seconds``, host inputs cycling over
+    ``rqs``; latency = submit call to the end of the poll that returns the C_l."""
+    import queue
+    import threading
+
+    from paper_2410_03632_gb300 import blast as bl
+    srv = bl.Server([plan], hbm_budget=32 << 30, max_slots=256)
+    reqs = [plan.request(rq) for rq in rqs]
+    P = bl.blast_npairs(rqs[0].n_clust, rqs[0].n_lens)
+    n = max(1, int(rate * seconds))
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, n)
+    sub_t, done_t, status = [0.0] * n, [0.0] * n, [0] * n
+    work = queue.Queue()
+    out = np.empty((P, plan.L))
+
+    def poller():
+        while True:
+            item = work.get()
+            if item is None:
+                return
+            i, t = item
+            status[i], _ = bl.blast_poll(srv.h, t, out.ctypes.data, -1)
+            done_t[i] = time.perf_counter()
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    nxt, busy = t0, 0
+    for i in range(n):
+        nxt += gaps[i]
+        while True:
+            d = nxt - time.perf_counter()
+            if d <= 0:
+                break
+            time.sleep(min(d, 5e-4))
+        sub_t[i] = time.perf_counter()
+        rc, t = bl.blast_submit(srv.h, 0, reqs[i % len(reqs)], prec)
+        while rc == bl.BLAST_EBUSY:  # admission pushed back: the wait counts as latency
+            busy += 1
+            time.sleep(1e-4)
+            rc, t = bl.blast_submit(srv.h, 0, reqs[i % len(reqs)], prec)
+        if rc != 0:
+            raise RuntimeError(f"blast_submit: {bl.blast_status_str(rc)}")
+        work.put((i, t))
+    work.put(None)
+    th.join()
+    srv.close()
+    if any(status):
+        raise RuntimeError("blast_poll failed")
+    lat = sorted((b - a) * 1e3 for a, b in zip(sub_t, done_t))
+    wall = max(done_t) - t0
+    return {"p50": lat[n // 2], "p99": lat[min(n - 1, int(0.99 * n))], "max": lat[-1], "requests": n,
+            "offered_req_s": rate, "served_req_s": n / wall, "busy_retries": busy, "precision": prec_name,
+            "what": "server (blast_submit/blast_poll, continuous batching, max 256 per batch), seeded Poisson "
+                    "arrivals, host inputs; submit to completed poll"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -361,6 +425,10 @@ def main():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--impl", default="blast", choices=["blast", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=2000.0,
+                    help="offered request rate of the serving-latency run (requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0,
+                    help="length of the serving-latency run (0 = skip)")
     ap.add_argument("--basis-cache", default=None,
                     help="file to load the FP64 basis from (or save it to after computing it)")
     args = ap.parse_args()

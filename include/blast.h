@@ -213,6 +213,40 @@ int blast_cl_noalloc(blast_plan *plan, const blast_request *req, double *cl_out,
  * weights, partial sums, outputs); the server admits requests against it. */
 size_t blast_request_footprint(const blast_plan *plan, const blast_request *req);
 
+/* ---------------------------------------------------------------- serving
+ * A server evaluates requests submitted from any host thread by continuous
+ * batching over one or more resident plans (Sec. 3.3: the basis is computed
+ * once and reused for every cosmology; requests share it).
+ *
+ * blast_server_create: plans[0..n_plans) stay owned by the caller, must outlive
+ *   the server, and must not be used by other calls while it exists (its worker
+ *   uses their work space).  hbm_budget bounds the summed
+ *   blast_request_footprint of the requests admitted and not yet evaluated;
+ *   max_slots bounds a batch.  One worker thread and one stream per plan.
+ * blast_submit: copies the request's inputs (host or device, per mem_space)
+ *   into server-owned pinned memory before it returns, checks them as
+ *   blast_cl would (BLAST_EINVAL, BLAST_ENOBASIS), and admits the request:
+ *   BLAST_EBUSY when the budget or the queue (16 max_slots) is full now (retry
+ *   later), BLAST_ENOMEM when the request alone exceeds the budget.  *ticket
+ *   identifies it.  The oldest waiting request fixes the (plan, precision) of
+ *   the next batch; waiting requests with the same pair join it in arrival
+ *   order, up to max_slots.  A request's C_l does not depend on its batch
+ *   (FP64 bitwise equal to blast_cl).  A batch that fails is re-run request
+ *   by request, so a bad request fails alone.
+ * blast_poll: waits up to timeout_us microseconds (negative = until done) for
+ *   the ticket.  Not done: BLAST_ENOTREADY, *done = 0.  Done: *done = 1, the
+ *   request's status is returned, on success C[npairs][n_sel] is copied to
+ *   cl_out (host or device memory), and the ticket is retired (polling it
+ *   again is BLAST_EINVAL, as is an unknown ticket).
+ * blast_server_destroy: evaluates the requests still waiting, frees results
+ *   never polled, and frees the server; no call on the server may run
+ *   concurrently with it. */
+int blast_server_create(blast_plan *const *plans, int n_plans, size_t hbm_budget, int max_slots,
+                        blast_server **out);
+int blast_submit(blast_server *server, int plan_idx, const blast_request *req, int precision, uint64_t *ticket);
+int blast_poll(blast_server *server, uint64_t ticket, double *cl_out, int *done, int64_t timeout_us);
+int blast_server_destroy(blast_server *server);
+
 /* Kernel classes of the evaluation path, for blast_profile_read. */
 #define BLAST_K_FIT 0         /* step (a0): Chebyshev fit */
 #define BLAST_K_WEIGHTS 1     /* quadrature weights U, V with growth folded in */

@@ -86,6 +86,10 @@ def lib():
             L.blast_profile_enable.argtypes = [P, i]
             L.blast_profile_read.argtypes = [P, i, _dp, ctypes.POINTER(ctypes.c_longlong)]
             L.blast_profile_reset.argtypes = [P]
+            L.blast_server_create.argtypes = [ctypes.POINTER(P), i, sz, i, ctypes.POINTER(P)]
+            L.blast_submit.argtypes = [P, i, ctypes.POINTER(blast_request), i, ctypes.POINTER(ctypes.c_uint64)]
+            L.blast_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(i), ctypes.c_int64]
+            L.blast_server_destroy.argtypes = [P]
             _LIB = L
     return _LIB
 
@@ -149,6 +153,32 @@ def blast_status_str(rc):
 
 BLAST_K_FIT, BLAST_K_WEIGHTS, BLAST_K_CONTRACT, BLAST_K_CONTRACT_TC, BLAST_K_REDUCE = 0, 1, 2, 3, 4
 KERNEL_CLASS_NAMES = ["fit", "weights", "contract", "contract_tc", "reduce"]
+
+
+def blast_server_create(plan_handles, hbm_budget, max_slots):
+    arr = (_vp * len(plan_handles))(*plan_handles)
+    h = _vp()
+    _check(lib().blast_server_create(arr, len(plan_handles), hbm_budget, max_slots, ctypes.byref(h)),
+           "blast_server_create")
+    return h
+
+
+def blast_submit(h, plan_idx, req, precision):
+    """(status, ticket)."""
+    t = ctypes.c_uint64()
+    rc = lib().blast_submit(h, plan_idx, ctypes.byref(req), precision, ctypes.byref(t))
+    return rc, t.value
+
+
+def blast_poll(h, ticket, out_ptr, timeout_us=-1):
+    """(status, done)."""
+    d = ctypes.c_int()
+    rc = lib().blast_poll(h, ticket, out_ptr, ctypes.byref(d), timeout_us)
+    return rc, d.value
+
+
+def blast_server_destroy(h):
+    return lib().blast_server_destroy(h)
 
 
 def blast_profile_enable(h, enable):
@@ -269,3 +299,34 @@ class Plan:
         outs = [np.empty((blast_npairs(rq.n_clust, rq.n_lens), self.n_sel(s))) for rq, s in zip(rqs, ell_sels)]
         _check(blast_cl_batch(self.h, reqs, precision, [o.ctypes.data for o in outs], 0), "blast_cl_batch")
         return outs
+
+
+class Server:
+    """Owns one ``blast_server`` over ``plans`` (``Plan`` objects that must
+    outlive it and are not used elsewhere meanwhile)."""
+
+    def __init__(self, plans, hbm_budget=8 << 30, max_slots=256):
+        self.plans = list(plans)
+        self.h = blast_server_create([p.h for p in self.plans], hbm_budget, max_slots)
+
+    def submit(self, plan_idx, rq, precision=BLAST_FP64, ell_sel=None):
+        """(status, ticket) for a synth.Request; inputs are copied before it returns."""
+        r = self.plans[plan_idx].request(rq, ell_sel)
+        return blast_submit(self.h, plan_idx, r, precision)
+
+    def poll(self, ticket, shape, timeout_us=-1):
+        """(status, C or None)."""
+        out = np.empty(shape)
+        rc, done = blast_poll(self.h, ticket, out.ctypes.data, timeout_us)
+        return rc, (out if done and rc == BLAST_OK else None)
+
+    def close(self):
+        if self.h:
+            blast_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

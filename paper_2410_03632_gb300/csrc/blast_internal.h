@@ -133,4 +133,6 @@ bool tc_supported(const blast_plan *p);
 
 // Host helpers
 int plan_alloc_basis(blast_plan *p, unsigned mask);
+int request_check(const blast_plan *p, const blast_request *r);  // the checks of blast_cl
+int request_n_sel(const blast_plan *p, const blast_request *r);  // ells selected by the mask
 double host_now();

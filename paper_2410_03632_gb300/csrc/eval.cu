@@ -320,6 +320,15 @@ bool ell_selected(const blast_request *r, int e)
 
 }  // namespace
 
+int request_check(const blast_plan *p, const blast_request *r) { return validate_request(p, r); }
+
+int request_n_sel(const blast_plan *p, const blast_request *r)
+{
+    int nsel = 0;
+    for (int e = 0; e < p->L; e++) nsel += ell_selected(r, e);
+    return nsel;
+}
+
 size_t request_in_doubles(const blast_plan *p, int ntr, int nptab)
 {
     return (size_t)ntr * (p->X + p->Q) + p->X + p->Q + 2 * (size_t)nptab;
