@@ -114,14 +114,19 @@ def lensing_kernel_over_chi2(cosmo: Cosmology, mu, sigma, chi, nzg: int = 20001)
         return np.where(chi > 0.0, W / chi ** 2, 0.0)
 
 
-def pk_table(n2=-2.0, a_w=0.05, phi=0.0, s8=0.8, n=256, kmin=1e-4, kmax=10.0):
-    """Smooth broken power law with damped BAO-like wiggles."""
-    k = np.geomspace(kmin, kmax, n)
+def pk_eval(k, n2=-2.0, a_w=0.05, phi=0.0, s8=0.8):
+    """Smooth broken power law with damped BAO-like wiggles, at any k (h/Mpc)."""
+    k = np.asarray(k, dtype=np.float64)
     kp, rw = 0.02, 105.0
     A = 5e4 * (s8 / 0.8) ** 2
     x = k / kp
-    p = A * x / (1.0 + x ** (1.0 - n2)) * (1.0 + a_w * np.sin(k * rw + phi) * np.exp(-(k / 0.3) ** 2))
-    return k, p
+    return A * x / (1.0 + x ** (1.0 - n2)) * (1.0 + a_w * np.sin(k * rw + phi) * np.exp(-(k / 0.3) ** 2))
+
+
+def pk_table(n2=-2.0, a_w=0.05, phi=0.0, s8=0.8, n=256, kmin=1e-4, kmax=10.0):
+    """pk_eval tabulated on n log-spaced points."""
+    k = np.geomspace(kmin, kmax, n)
+    return k, pk_eval(k, n2, a_w, phi, s8)
 
 
 # ----------------------------------------------------------------------------- workloads
