@@ -41,6 +41,30 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+# --------------------------------------------------------------------------- replicas
+# The path shards by cosmology: every rank evaluates its own batch on its own
+# GPU with no exchange; the job's time is the slowest rank's.
+def replica_request_ids(rank, batch):
+    """Seeded cosmology indices of a rank's batch (disjoint across ranks)."""
+    return [1 + i + rank * batch for i in range(batch)]
+
+
+def max_over_ranks(x, world, device=None):
+    """The largest value over ranks (an all-reduce MAX); x itself at world 1."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, batch, steps, seconds):
+    """C_l-sets per second of the whole job: every rank's batches over the slowest rank's time."""
+    return world * batch * steps / seconds
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -179,7 +203,7 @@ def run_blast(args):
             bl.blast_basis_save(plan.h, cache)
     chi, R, _ = plan.nodes()
     B = args.batch
-    rqs = [synth.config_request("c1", chi, R, 1 + i + rank * B) for i in range(B)]
+    rqs = [synth.config_request("c1", chi, R, i) for i in replica_request_ids(rank, B)]
     fields = ["kern_chi", "kern_Rchi", "growth_chi", "growth_Rchi", "k_tab", "p_tab"]
     dev_arrays = [{f: torch.from_numpy(np.ascontiguousarray(getattr(rq, f))).to(dev) for f in fields} for rq in rqs]
     reqs = [plan.request(rq, device_arrays=d) for rq, d in zip(rqs, dev_arrays)]
@@ -217,11 +241,7 @@ def run_blast(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         prof = {}
         for c, name in enumerate(bl.KERNEL_CLASS_NAMES):
             prof[name] = bl.blast_profile_read(plan.h, c)
@@ -313,18 +333,14 @@ def run_blast(args):
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
 
     serve = None
     if args.serve_seconds > 0 and rank == 0:
         serve = serve_latency(plan, rqs, prec_main, dtype_main, args.serve_rate, args.serve_seconds)
 
     launches = sum(prof_main[n][1] for n in bl.KERNEL_CLASS_NAMES)
-    value = world * B * args.steps / (ms_main * 1e-3)
+    value = job_throughput(world, B, args.steps, ms_main * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_main / args.steps, "higher_is_better": True,
@@ -332,7 +348,7 @@ def run_blast(args):
         "config": {"workload": WORKLOAD, "batch_per_gpu": B, "precision": dtype_main,
                    "l2": "inputs larger than L2 (basis tables 0.8-1.6 GB per step)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "fp64": {"value": world * B * k64 / (ms_64 * 1e-3), "unit": UNIT, "ms_per_step": ms_64 / k64,
+        "fp64": {"value": job_throughput(world, B, k64, ms_64 * 1e-3), "unit": UNIT, "ms_per_step": ms_64 / k64,
                  "dtype": "f64"},
         "err_vs_fp64": {"max_eij": err, "bound": 1e-4,
                         "def": "|C-C_fp64|/sqrt(C_ii C_jj), every cosmology of the batch, all pairs and ells"},
@@ -340,7 +356,7 @@ def run_blast(args):
         "single_call_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                    "what": "one blast_cl call, one cosmology, FP32 path, device inputs"},
         "roofline": roof,
-        "e2e": {"value": world * B * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_throughput(world, B, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "kernels_ms_per_step": {n: prof_main[n][0] / args.steps for n in bl.KERNEL_CLASS_NAMES
