@@ -572,8 +572,6 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                         // (FMA) and each addition's rounding error is kept (two-sum), so the
                         // sum survives the cancellation of oscillating w
                         f32x2 An[kNB], Bn[kNB];
-#pragma unroll
-                        for (int j = 0; j < kNB; j++) { An[j] = 0ull; Bn[j] = 0ull; }
                         // levels of the next column pair load while this pair is summed
                         uint32_t D[kS][2];
 #pragma unroll
@@ -608,9 +606,14 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                                 const f32x2 v = vme[(j * (kHC / 2) + cp) * (128 * kEP)];
                                 const f32x2 prn = mul2(v, mn);                  // -fl(v m)
                                 const f32x2 pe = fma2(v, lo, fma2(v, m, prn));  // v lo + (v m - fl(v m))
-                                f32x2 se;
-                                two_sum2(An[j], prn, An[j], se);
-                                Bn[j] = add2(Bn[j], sub2(se, pe));
+                                if (cp == 0) {  // first column pair: the sums start here, exactly
+                                    An[j] = prn;
+                                    Bn[j] = neg2(pe);
+                                } else {
+                                    f32x2 se;
+                                    two_sum2(An[j], prn, An[j], se);
+                                    Bn[j] = add2(Bn[j], sub2(se, pe));
+                                }
                             }
                         }
                         // both lanes into one pair per tracer: S = -(An.x + An.y) - (Bn.x + Bn.y)
@@ -672,23 +675,43 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     }
 }
 
+// A thread's staging slot of k_reduce_tc in float2 units: RT MT pairs and the
+// kNB + kNB chi weights, rounded up to 16 bytes so every slot is 16-byte aligned.
+__host__ __device__ __forceinline__ int reduce_slot_f2(int RT, int MT) { return (RT * MT + kNB + 1) & ~1; }
+
+// Asynchronous global -> shared copies (cp.async): 16, 8 or 4 bytes each,
+// visible to the issuing thread after the matching wait_group.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // Sum over R tiles and chi nodes for the tensor-core path, one thread per
 // (cosmology, type, ell, chi chunk) accumulating every tracer pair (i, j):
 //   s_j(a) = sum_rt Y(t, l, a, rt, j)          (pairs (hi, lo), two-sum)
 //   C_ij(l) = N_AB(l) sum_a U_i(a) s_j(a)      (exact products, two-sum)
-// A block is 32 cosmologies x kRedChunks chi chunks (one warp each); the chunks
-// are added in a tree through shared memory.  The loads of the next group of
-// R tiles are in flight while the current group is summed.
-constexpr int kRedChunks = 16;  // chi chunks per (cosmology, type, ell): one warp each
-constexpr int kRedRT = 2;       // R tiles per load group
-
-__global__ void __launch_bounds__(32 * kRedChunks, 1)
+// A block is 32 cosmologies x W chi chunks (one warp each).  Each thread
+// streams its own R-tile pairs and chi weights of the next STG - 1 chi nodes
+// into its own shared-memory slots with cp.async while it sums the current
+// one, so enough bytes are in flight to keep HBM busy; the chunks are then
+// added in a tree through the same shared memory.
+template <int W, int STG>
+__global__ void __launch_bounds__(32 * W, 2)
 k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const float *__restrict__ UT,
             const float *__restrict__ UTl, int n, int Bpad, int X, int L, const int *__restrict__ esel, int n_esel,
             int RT, int MT, const double *__restrict__ pref)
 {
-    extern __shared__ float red_raw[];  // [kRedChunks / 2][32][2 kNB kNB]
-    float(*red)[32][2 * kNB * kNB] = reinterpret_cast<float(*)[32][2 * kNB * kNB]>(red_raw);
+    extern __shared__ __align__(16) unsigned char red_smem[];
     const int lane = threadIdx.x & 31, chunk = threadIdx.x >> 5;
     const int b = blockIdx.x * 32 + lane;
     const int es = blockIdx.y, t = blockIdx.z;
@@ -698,84 +721,84 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
     const int e = esel[es];
     const int col = rq ? rq->e_out[e] : -1;
     const bool active = rq && nA > 0 && nB > 0 && col >= 0;
+    // per thread and stage: RT MT pairs (hi, lo), then U hi[kNB], U lo[kNB]
+    const int RTMT = RT * MT;
+    const int slot_f2 = reduce_slot_f2(RT, MT);
+    float2 *my = reinterpret_cast<float2 *>(red_smem) + ((size_t)chunk * STG * 32 + lane) * slot_f2;
+    auto stage_ptr = [&](int st) { return my + (size_t)st * 32 * slot_f2; };
+    const int per = (X + W - 1) / W;
+    const int a0 = chunk * per, a1 = min(X, a0 + per);
+    const int cnt = active ? max(0, a1 - a0) : 0;
+    const float2 *Yb = reinterpret_cast<const float2 *>(Y) + ((size_t)t * n_esel + es) * (size_t)X * n * RTMT +
+                       (size_t)b * RTMT;
+    const bool even = (RTMT & 1) == 0;  // 16-byte copies when each thread's pairs are 16-byte aligned
+    auto issue = [&](int k) {           // copies of chi node a0 + k into stage k % STG
+        if (k < cnt) {
+            float2 *d = stage_ptr(k % STG);
+            const float2 *y = Yb + (size_t)(a0 + k) * n * RTMT;
+            if (even)
+                for (int i = 0; i < RTMT; i += 2) cp_async16(d + i, y + i);
+            else
+                for (int i = 0; i < RTMT; i++) cp_async8(d + i, y + i);
+            float *u = reinterpret_cast<float *>(d + RTMT);
+            for (int i = 0; i < nA; i++) {
+                const size_t ui = ((size_t)(offA + i) * X + a0 + k) * Bpad + b;
+                cp_async4(u + i, UT + ui);
+                cp_async4(u + kNB + i, UTl + ui);
+            }
+        }
+        cp_async_commit();  // every thread commits every step: group counts stay uniform
+    };
     float Zh[kNB][kNB], Zl[kNB][kNB];
 #pragma unroll
     for (int i = 0; i < kNB; i++)
 #pragma unroll
         for (int j = 0; j < kNB; j++) { Zh[i][j] = 0.f; Zl[i][j] = 0.f; }
-    const int per = (X + kRedChunks - 1) / kRedChunks;
-    const int a0 = chunk * per, a1 = min(X, a0 + per);
-    const int ngrp = (RT + kRedRT - 1) / kRedRT;
-    const int total = active ? max(0, a1 - a0) * ngrp : 0;
-    // (hi, lo) of R tile rt, tracer j, at chi node a: Yb[(a n) RT MT + rt MT + j]
-    const float2 *Yb = reinterpret_cast<const float2 *>(Y) + ((size_t)t * n_esel + es) * (size_t)X * n * RT * MT +
-                       (size_t)b * RT * MT;
-    auto load_group = [&](int it, float2 (&v)[kRedRT][kNB]) {
-        const int a = a0 + it / ngrp, rt0 = (it % ngrp) * kRedRT;
-        const float2 *y = Yb + (size_t)a * n * RT * MT;
 #pragma unroll
-        for (int k = 0; k < kRedRT; k++)
+    for (int k = 0; k < STG - 1; k++) issue(k);
+    for (int k = 0; k < per; k++) {
+        issue(k + STG - 1);
+        cp_async_wait<STG - 1>();  // node a0 + k has landed
+        if (k >= cnt) continue;
+        const float2 *v = stage_ptr(k % STG);
+        float sh[kNB], sl[kNB];
 #pragma unroll
-            for (int j = 0; j < kNB; j++)
-                v[k][j] = (rt0 + k < RT && j < nB) ? __ldg(y + (size_t)(rt0 + k) * MT + j) : make_float2(0.f, 0.f);
-    };
-    float2 cur[kRedRT][kNB];
-    if (total > 0) load_group(0, cur);
-    float sh[kNB], sl[kNB];
-#pragma unroll
-    for (int j = 0; j < kNB; j++) { sh[j] = 0.f; sl[j] = 0.f; }
-    float uh[kNB], ul[kNB];
-    for (int it = 0; it < total; it++) {
-        const int a = a0 + it / ngrp, g = it % ngrp;
-        if (g == 0) {  // chi weights of this node, in flight with the R tiles
-#pragma unroll
-            for (int i = 0; i < kNB; i++) {
-                const size_t ui = ((size_t)(offA + i) * X + a) * Bpad + b;
-                uh[i] = (i < nA) ? __ldg(UT + ui) : 0.f;
-                ul[i] = (i < nA) ? __ldg(UTl + ui) : 0.f;
-            }
-        }
-        float2 nxt[kRedRT][kNB];
-        if (it + 1 < total) load_group(it + 1, nxt);
-#pragma unroll
-        for (int k = 0; k < kRedRT; k++)
+        for (int j = 0; j < kNB; j++) { sh[j] = 0.f; sl[j] = 0.f; }
+        for (int rt = 0; rt < RT; rt++) {
 #pragma unroll
             for (int j = 0; j < kNB; j++) {
-                float se;
-                two_sum(sh[j], cur[k][j].x, sh[j], se);
-                sl[j] = __fadd_rn(sl[j], __fadd_rn(se, cur[k][j].y));
-            }
-        if (g == ngrp - 1) {
-            float sv[kNB], sle[kNB];
-#pragma unroll
-            for (int j = 0; j < kNB; j++) {
-                two_sum(sh[j], sl[j], sv[j], sle[j]);
-                sh[j] = 0.f;
-                sl[j] = 0.f;
-            }
-#pragma unroll
-            for (int i = 0; i < kNB; i++) {
-                if (i >= nA) continue;
-#pragma unroll
-                for (int j = 0; j < kNB; j++) {
-                    if (j >= nB) continue;
-                    const float pr = __fmul_rn(uh[i], sv[j]);
-                    const float pe = fmaf(uh[i], sle[j], fmaf(ul[i], sv[j], fmaf(uh[i], sv[j], -pr)));
+                if (j < nB) {
+                    const float2 y = v[rt * MT + j];
                     float se;
-                    two_sum(Zh[i][j], pr, Zh[i][j], se);
-                    Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, pe));
+                    two_sum(sh[j], y.x, sh[j], se);
+                    sl[j] = __fadd_rn(sl[j], __fadd_rn(se, y.y));
                 }
             }
         }
-        if (it + 1 < total) {
+        const float *u = reinterpret_cast<const float *>(v + RTMT);
+        float sv[kNB], sle[kNB];
 #pragma unroll
-            for (int k = 0; k < kRedRT; k++)
+        for (int j = 0; j < kNB; j++) two_sum(sh[j], sl[j], sv[j], sle[j]);
 #pragma unroll
-                for (int j = 0; j < kNB; j++) cur[k][j] = nxt[k][j];
+        for (int i = 0; i < kNB; i++) {
+            if (i >= nA) continue;
+            const float uh = u[i], ul = u[kNB + i];
+#pragma unroll
+            for (int j = 0; j < kNB; j++) {
+                if (j >= nB) continue;
+                const float pr = __fmul_rn(uh, sv[j]);
+                const float pe = fmaf(uh, sle[j], fmaf(ul, sv[j], fmaf(uh, sv[j], -pr)));
+                float se;
+                two_sum(Zh[i][j], pr, Zh[i][j], se);
+                Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, pe));
+            }
         }
     }
+    cp_async_wait<0>();
+    __syncthreads();  // the staging slots become the tree's exchange area
     // tree over the chi chunks: the upper half of the warps hands its pairs down
-    for (int half = kRedChunks / 2; half >= 1; half >>= 1) {
+    float(*red)[32][2 * kNB * kNB] = reinterpret_cast<float(*)[32][2 * kNB * kNB]>(red_smem);
+    for (int half = W / 2; half >= 1; half >>= 1) {
         if (chunk >= half && chunk < 2 * half) {
 #pragma unroll
             for (int i = 0; i < kNB; i++)
@@ -815,6 +838,14 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
             rq->cl[(size_t)p * rq->n_sel + col] = out;
         }
     }
+}
+
+// Shared memory of k_reduce_tc<W, STG>: the staging slots, at least the tree's area.
+size_t reduce_smem(int W, int STG, int RT, int MT)
+{
+    const size_t stage = (size_t)W * STG * 32 * reduce_slot_f2(RT, MT) * sizeof(float2);
+    const size_t tree = (size_t)(W / 2) * 32 * 2 * kNB * kNB * sizeof(float);
+    return stage > tree ? stage : tree;
 }
 
 // ---------------------------------------------------------------- host side
@@ -937,11 +968,21 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
     const int Bpad = (n + kM - 1) / kM * kM;
     const float *UT = reinterpret_cast<const float *>(p->ws.tc.as<uint16_t>() + (size_t)kS * Bpad * p->Kp) + Bpad;
     const float *UTl = UT + (size_t)(p->max_clust + p->max_lens) * p->X * Bpad;
+    const int RT = p->Rn / kQT, MT = p->max_tr;
     dim3 grid((n + 31) / 32, n_esel, 3);
-    const int smem = kRedChunks / 2 * 32 * 2 * kNB * kNB * (int)sizeof(float);
-    BL_CUDA(cudaFuncSetAttribute(k_reduce_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_reduce_tc<<<grid, 32 * kRedChunks, smem, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel, n_esel,
-                                     p->Rn / kQT, p->max_tr, p->d_pref);
+    constexpr size_t kSmemMax = 220 * 1024;
+    if (reduce_smem(8, 2, RT, MT) <= kSmemMax / 2) {  // 8 chi chunks, 2 stages, two blocks per SM
+        const int smem = (int)reduce_smem(8, 2, RT, MT);
+        BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_reduce_tc<8, 2><<<grid, 32 * 8, smem, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel,
+                                                     n_esel, RT, MT, p->d_pref);
+    } else {  // long R-tile rows (n_R up to 512): 4 chunks, 2 stages
+        const int smem = (int)reduce_smem(4, 2, RT, MT);
+        if ((size_t)smem > kSmemMax) return BLAST_EINVAL;
+        BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_reduce_tc<4, 2><<<grid, 32 * 4, smem, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel,
+                                                     n_esel, RT, MT, p->d_pref);
+    }
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
 }
