@@ -134,11 +134,25 @@ __global__ void k_weights(ReqDev *reqs, int X, int Rn, const double *__restrict_
 {
     ReqDev &rq = reqs[blockIdx.y];
     const int ntr = rq.n_clust + rq.n_lens, Q = X * Rn;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntr * Q; i += gridDim.x * blockDim.x) {
-        int q = i % Q, r = q % Rn;
-        double vv = wR[r] * rq.growth_Rchi[q] * rq.kern_Rchi[i];
-        if (want_v64) rq.V64[i] = vv;
-        if (want32) rq.V32[i] = (float)vv;
+    // one thread per chi-R node: its growth factor is read once for every tracer,
+    // and each group of tracer values is loaded before any is stored (inputs may
+    // be host memory read over the host link, where latency dominates)
+    constexpr int kG = 8;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+        const double g = wR[q % Rn] * rq.growth_Rchi[q];
+        for (int t0 = 0; t0 < ntr; t0 += kG) {
+            double k[kG];
+#pragma unroll
+            for (int u = 0; u < kG; u++) k[u] = (t0 + u < ntr) ? rq.kern_Rchi[(size_t)(t0 + u) * Q + q] : 0.0;
+#pragma unroll
+            for (int u = 0; u < kG; u++) {
+                if (t0 + u >= ntr) break;
+                const size_t i = (size_t)(t0 + u) * Q + q;
+                const double vv = g * k[u];
+                if (want_v64) rq.V64[i] = vv;
+                if (want32) rq.V32[i] = (float)vv;
+            }
+        }
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntr * X; i += gridDim.x * blockDim.x) {
         int a = i % X;
@@ -246,7 +260,7 @@ int launch_fit(blast_plan *p, ReqDev *dreq, int nreq, cudaStream_t s)
 
 int launch_weights(blast_plan *p, ReqDev *dreq, int nreq, int want32, cudaStream_t s, int want_v64)
 {
-    dim3 grid((p->Q * 2 + 255) / 256 < 1024 ? (p->Q * 2 + 255) / 256 : 1024, nreq);
+    dim3 grid((p->Q + 255) / 256 < 1024 ? (p->Q + 255) / 256 : 1024, nreq);
     k_weights<<<grid, 256, 0, s>>>(dreq, p->X, p->Rn, p->d_chi, p->d_wchi, p->d_wR, want32, want_v64);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
