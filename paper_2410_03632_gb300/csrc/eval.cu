@@ -370,6 +370,9 @@ extern "C" size_t blast_request_footprint(const blast_plan *p, const blast_reque
 // tables, pageable != 0) any host address.
 static const void *device_view(const void *hp, int pageable)
 {
+    // a GPU that walks the host page tables reads any host address as it is:
+    // no query (one per array costs about half a microsecond of host time)
+    if (pageable) return hp;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, hp) != cudaSuccess) {
         cudaGetLastError();
