@@ -219,6 +219,11 @@ def plan_spec(name: str) -> PlanSpec:
     elif name == "small":
         return PlanSpec(ell_list(11, 2, 120), 41, 40.0, 2400.0, 26, 0.2, 1.8, 35, 1e-4, 1.0, 1,
                         kquad_points(1e-4, 1.0, 2400.0, 1.8), 3, 2)
+    elif name == "c2s":
+        # the 10+10-bin grid's shapes (n_R = 192, order 96, 20 tracers, chi to 4100) on
+        # few ells and chi nodes with k_max = 1, so the oracle's basis takes seconds
+        return PlanSpec(np.array([2, 30, 120, 300], np.int32), 24, 26.0, 4100.0, 192, 0.2, 1.8, 96, 1e-4, 1.0, 1,
+                        kquad_points(1e-4, 1.0, 4100.0, 1.8), 10, 10)
     elif name == "tc":
         # tensor-core path shapes: n_R a multiple of 32, n_cheb <= 64, <= 5 tracers per kind
         return PlanSpec(ell_list(9, 2, 300), 21, 40.0, 2400.0, 64, 0.2, 1.8, 40, 1e-4, 1.0, 1,
@@ -232,7 +237,7 @@ def plan_spec(name: str) -> PlanSpec:
 def config_request(name: str, chi, R, idx: int = 0) -> Request:
     """The seeded request of a workload: seed 1000 + config + 7919 idx."""
     spec = plan_spec(name)
-    cfg = {"c0": 0, "c1": 1, "c2": 2, "tiny": 10, "small": 11, "tc": 12}[name]
+    cfg = {"c0": 0, "c1": 1, "c2": 2, "tiny": 10, "small": 11, "tc": 12, "c2s": 13}[name]
     rng = np.random.default_rng(1000 + cfg + 7919 * idx)
     ng, ns = spec.max_clust, spec.max_lens
     zb = {}

@@ -1,0 +1,86 @@
+"""Parity at the benchmark sizes, through the C ABI.
+
+- The 3x2pt 5+5-bin benchmark grid (64 ells to 1000, n_chi = n_R = 128, order
+  64, 65 537 k nodes), in the batch configuration the benchmark times: the
+  oracle computes the basis and C_l at l = 2 (a sampled output: every spectrum
+  of one ell); the GPU basis, FP64 C_l and tensor-core C_l of a batch of
+  cosmologies are compared with it.
+- The 10+10-bin grid's shapes (20 tracers, 210 spectra, order 96, n_R = 192)
+  on a few ells and chi nodes: FP64 C_l against the oracle for every spectrum
+  and ell; the tensor-core path, which serves at most 5 tracers per kind and
+  order 64, refuses the plan.
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2410_03632_gb300 import blast as bl
+from paper_2410_03632_gb300 import synth
+from tests.metrics import eij
+
+pytestmark = pytest.mark.gpu
+
+
+def _have_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+if not _have_gpu():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+
+def _grid(spec):
+    return orc.Grid(spec.ells, spec.n_chi, spec.chi_min, spec.chi_max, spec.n_R, spec.R_min, spec.R_max,
+                    spec.n_cheb, spec.k_min, spec.k_max, spec.n_kquad, spec.k_map)
+
+
+def test_benchmark_grid_sampled_at_ell_2():
+    spec = synth.plan_spec("c1")
+    plan = bl.Plan(spec)
+    try:
+        plan.precompute(bl.BASIS_ALL)
+        g = _grid(spec)
+        To = g.basis(ell_subset=g.ells[:1])                     # [3][1][N][Q], l = 2
+        Tg = plan.basis()[:, :1]
+        scale = np.max(np.abs(To), axis=-1, keepdims=True)
+        # both sides sum 65 537 oscillating FP64 terms in different orders (the
+        # oracle compensated): sqrt(65537) x 1.1e-16 x a cancellation of up to ~1e3
+        # is ~3e-11 of the row maximum (measured 4.0e-11)
+        assert np.max(np.abs(Tg - To) / np.where(scale > 0, scale, 1.0)) < 1e-10
+        chi, R, _ = plan.nodes()
+        rqs = [synth.config_request("c1", chi, R, 1 + i) for i in range(8)]
+        c64 = plan.cl_batch(rqs, bl.BLAST_FP64)
+        ctc = plan.cl_batch(rqs, bl.BLAST_BF16S)
+        for rq, a, b in zip(rqs, c64, ctc):
+            Co = g.cl(To, g.fit(rq.k_tab, rq.p_tab), 5, 5, rq.kern_chi, rq.kern_Rchi, rq.growth_chi,
+                      rq.growth_Rchi, ell_subset=g.ells[:1])
+            assert np.max(eij(a[:, :1], Co, 5, 5)) < 1e-10
+            assert np.max(eij(b[:, :1], Co, 5, 5)) < 1e-4
+    finally:
+        plan.close()
+
+
+def test_ten_plus_ten_bin_shapes_fp64():
+    spec = synth.plan_spec("c2s")
+    plan = bl.Plan(spec)
+    try:
+        plan.precompute(bl.BASIS_ALL)
+        g = _grid(spec)
+        To = g.basis()
+        chi, R, _ = plan.nodes()
+        rqs = [synth.config_request("c2s", chi, R, i) for i in range(3)]
+        outs = plan.cl_batch(rqs, bl.BLAST_FP64)
+        for rq, C in zip(rqs, outs):
+            assert C.shape == (210, spec.ells.size)
+            Co = g.cl(To, g.fit(rq.k_tab, rq.p_tab), 10, 10, rq.kern_chi, rq.kern_Rchi, rq.growth_chi,
+                      rq.growth_Rchi)
+            assert np.max(eij(C, Co, 10, 10)) < 1e-10
+        with pytest.raises(bl.BlastError) as ei:
+            plan.cl_batch(rqs[:1], bl.BLAST_BF16S)
+        assert ei.value.status == bl.BLAST_EINVAL
+    finally:
+        plan.close()

@@ -1,7 +1,7 @@
 """Parity of the CUDA path against the FP64 oracle, through the C ABI.
 
 Bars: basis T~ elementwise within 1e-11 of the row maximum; FP64 C_l within
-e_ij <= 1e-10 and FP32 / BF16x3 C_l within e_ij <= 1e-4 of the oracle, with
+e_ij <= 1e-10 and FP32 C_l within e_ij <= 1e-4 of the oracle, with
 e_ij = |dC_ij| / sqrt(C_ii C_jj) (auto-spectrum normalisation).
 """
 import numpy as np
