@@ -105,7 +105,11 @@ typedef struct {
 /* One cosmology.  Tracers 0..n_clust-1 are clustering, n_clust..n_clust+n_lens-1
  * lensing; kernels are the paper's calligraphic K of Eq. final_cls (lensing
  * kernels already divided by chi^2).  All arrays float64, row major, host or
- * device per mem_space, and only read during the call.
+ * device per mem_space.  When they are read: a call with host outputs waits for
+ * its stream, so every input is read before it returns; a call with device
+ * outputs is stream ordered, so device inputs, and pinned host inputs (copied
+ * with cudaMemcpyAsync), are read when the stream runs the call (pageable host
+ * inputs are staged before it returns) and must stay unchanged until then.
  *   kern_chi     [n_clust+n_lens][n_chi]          K at chi_a
  *   kern_Rchi    [n_clust+n_lens][n_chi*n_R]      K at R_r chi_a, index a*n_R + r
  *   growth_chi   [n_chi]                          D(chi_a)
