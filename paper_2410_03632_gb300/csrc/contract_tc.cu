@@ -21,9 +21,10 @@
 // the epilogue adds the levels with a cascade of fast two-sums, each exact for
 // operands on these grids, W 2^-32 = m + (e1 + e2 + e3 + e4), and scales by
 // 2^(ea + eT - 16).  The R sum that follows also cancels (w oscillates around
-// R = 1), so it runs on unevaluated pairs: exact products (FMA) and two-sum
-// accumulation, two columns at a time in packed FP32 pairs; the pairs reach
-// the chi sum intact.
+// R = 1), so it runs on unevaluated pairs: exact products (FMA), two products
+// (columns two R nodes apart) added plainly, and two-sum accumulation of those
+// sums, two columns at a time in packed FP32 pairs; the pairs reach the chi
+// sum intact.
 //
 // Warp roles (576 threads): warp 0 issues TMA loads of the basis slices,
 // warp 1 owns TMEM and issues tcgen05.mma (A = coefficient slices resident in
@@ -187,10 +188,12 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
-// Two consecutive 32-bit columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&r)[2])
+// Four consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
 }
 
 // Knuth's two-sum: s + e == a + b exactly, s = fl(a + b).
@@ -269,16 +272,19 @@ __device__ __forceinline__ void two_sum2(f32x2 a, f32x2 b, f32x2 &s, f32x2 &e)
     s = ss;
 }
 
-// Wait for this thread's TMEM loads; the registers they fill are operands, so
-// no use of them can move above the wait.
-__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[BLAST_TC_SLICES][2])
+// Wait for this thread's TMEM loads of four columns per level; the registers
+// they fill are operands, so no use of them can move above the wait.
+__device__ __forceinline__ void tmem_wait_ld4(uint32_t (&r)[BLAST_TC_SLICES][4])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[1][0]), "+r"(r[1][1]), "+r"(r[2][0]), "+r"(r[2][1]),
-                   "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[4][0]), "+r"(r[4][1])
+                 : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[1][0]), "+r"(r[1][1]),
+                   "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]),
+                   "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]), "+r"(r[4][0]), "+r"(r[4][1]),
+                   "+r"(r[4][2]), "+r"(r[4][3])
                  :
                  : "memory");
 }
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -572,20 +578,17 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                         // (FMA) and each addition's rounding error is kept (two-sum), so the
                         // sum survives the cancellation of oscillating w
                         f32x2 An[kNB], Bn[kNB];
-                        // levels of the next column pair load while this pair is summed
-                        uint32_t D[kS][2];
+                        // four columns (two packed pairs) per step: pair A = columns c0, c0+1
+                        // in lanes x, y; pair B = c0+2, c0+3.  Each lane's two exact products
+                        // (columns two R nodes apart) are added plainly, and that sum enters
+                        // the compensated sum
 #pragma unroll
-                        for (int lev = 0; lev < kS; lev++) tmem_ld2(tcol + lev * kQT, D[lev]);
+                        for (int c0 = 0; c0 < kHC; c0 += 4) {
+                            uint32_t D[kS][4];
 #pragma unroll
-                        for (int cp = 0; cp < kHC / 2; cp++) {
-                            tmem_wait_ld(D);
-                            f32x2 d[kS];
-#pragma unroll
-                            for (int lev = 0; lev < kS; lev++) d[lev] = pk2(__uint_as_float(D[lev][0]), __uint_as_float(D[lev][1]));
-                            if (cp + 1 < kHC / 2) {
-#pragma unroll
-                                for (int lev = 0; lev < kS; lev++) tmem_ld2(tcol + lev * kQT + 2 * (cp + 1), D[lev]);
-                            } else {  // every level of this buffer is in registers: release it
+                            for (int lev = 0; lev < kS; lev++) tmem_ld4(tcol + lev * kQT + c0, D[lev]);
+                            tmem_wait_ld4(D);
+                            if (c0 + 4 == kHC) {  // every level of this buffer is in registers: release it
                                 tc_fence_before();
                                 mbar_arrive(&tempty[buf]);
                             }
@@ -594,24 +597,35 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                             // every fast two-sum of the cascade is exact:
                             // W 2^(eT - eG - 32) = m + (e1 + e2 + e3 + e4), one rounding in the
                             // low part only
-                            f32x2 m, e1, e2, e3, e4;
-                            fast_two_sum2(d[0], d[1], m, e1);
-                            fast_two_sum2(m, d[2], m, e2);
-                            fast_two_sum2(m, d[3], m, e3);
-                            fast_two_sum2(m, d[4], m, e4);
-                            const f32x2 lo = add2(add2(e1, e2), add2(e3, e4));
-                            const f32x2 mn = neg2(m);
+                            f32x2 m[2], lo[2];
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                f32x2 d[kS];
+#pragma unroll
+                                for (int lev = 0; lev < kS; lev++)
+                                    d[lev] = pk2(__uint_as_float(D[lev][2 * h]), __uint_as_float(D[lev][2 * h + 1]));
+                                f32x2 e1, e2, e3, e4;
+                                fast_two_sum2(d[0], d[1], m[h], e1);
+                                fast_two_sum2(m[h], d[2], m[h], e2);
+                                fast_two_sum2(m[h], d[3], m[h], e3);
+                                fast_two_sum2(m[h], d[4], m[h], e4);
+                                lo[h] = add2(add2(e1, e2), add2(e3, e4));
+                            }
+                            const f32x2 mn0 = neg2(m[0]), mn1 = neg2(m[1]);
 #pragma unroll
                             for (int j = 0; j < kNB; j++) {
-                                const f32x2 v = vme[(j * (kHC / 2) + cp) * (128 * kEP)];
-                                const f32x2 prn = mul2(v, mn);                  // -fl(v m)
-                                const f32x2 pe = fma2(v, lo, fma2(v, m, prn));  // v lo + (v m - fl(v m))
-                                if (cp == 0) {  // first column pair: the sums start here, exactly
-                                    An[j] = prn;
+                                const f32x2 v0 = vme[(j * (kHC / 2) + c0 / 2) * (128 * kEP)];
+                                const f32x2 v1 = vme[(j * (kHC / 2) + c0 / 2 + 1) * (128 * kEP)];
+                                const f32x2 p0 = mul2(v0, mn0), p1 = mul2(v1, mn1);  // -fl(v m)
+                                const f32x2 e0 = fma2(v0, lo[0], fma2(v0, m[0], p0));  // v lo + (v m - fl(v m))
+                                const f32x2 e1 = fma2(v1, lo[1], fma2(v1, m[1], p1));
+                                const f32x2 ps = add2(p0, p1), pe = add2(e0, e1);
+                                if (c0 == 0) {  // the sums start here
+                                    An[j] = ps;
                                     Bn[j] = neg2(pe);
                                 } else {
                                     f32x2 se;
-                                    two_sum2(An[j], prn, An[j], se);
+                                    two_sum2(An[j], ps, An[j], se);
                                     Bn[j] = add2(Bn[j], sub2(se, pe));
                                 }
                             }
