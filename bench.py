@@ -37,6 +37,13 @@ WORKLOAD = ("3x2pt, 5 clustering + 5 lensing bins (55 spectra), 64 log-spaced el
             "n_chi=128, n_R=128 (R in [0.2,1.8]), Chebyshev order 64, n_kquad=65537")
 
 
+def workload_config(batch, world):
+    """The workload both arms report (the arithmetic type is the line's dtype)."""
+    return {"workload": WORKLOAD, "batch_per_gpu": batch,
+            "l2": "inputs larger than L2 (basis tables 0.8-1.6 GB per step)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
@@ -159,7 +166,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": workload_config(args.batch, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -346,9 +353,7 @@ def run_blast(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_main / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_main, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch_per_gpu": B, "precision": dtype_main,
-                   "l2": "inputs larger than L2 (basis tables 0.8-1.6 GB per step)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": workload_config(B, world),
         "fp64": {"value": job_throughput(world, B, k64, ms_64 * 1e-3), "unit": UNIT, "ms_per_step": ms_64 / k64,
                  "dtype": "f64"},
         "err_vs_fp64": {"max_eij": err, "bound": 1e-4,
