@@ -1,5 +1,8 @@
 """Parity at the benchmark sizes, through the C ABI.
 
+- The plain FP64 1+1-bin grid (16 ells to 200, n_chi = n_R = 64, order 32,
+  65 537 k nodes) at full size, sampled at four ells: FP64 and tensor-core C_l
+  of two cosmologies against the oracle.
 - The 3x2pt 5+5-bin benchmark grid (64 ells to 1000, n_chi = n_R = 128, order
   64, 65 537 k nodes), in the batch configuration the benchmark times: the
   oracle computes the basis and C_l at l = 2 (a sampled output: every spectrum
@@ -84,3 +87,26 @@ def test_ten_plus_ten_bin_shapes_fp64():
         assert ei.value.status == bl.BLAST_EINVAL
     finally:
         plan.close()
+
+
+def test_one_plus_one_bin_grid_sampled_at_four_ells():
+    spec = synth.plan_spec("c0")
+    plan = bl.Plan(spec)
+    try:
+        plan.precompute(bl.BASIS_ALL)
+        g = _grid(spec)
+        sel = [0, 6, 11, 15]                                   # l = 2, 13, 59, 200
+        To = g.basis(ell_subset=g.ells[sel])
+        chi, R, _ = plan.nodes()
+        rqs = [synth.config_request("c0", chi, R, i) for i in range(2)]
+        c64 = plan.cl_batch(rqs, bl.BLAST_FP64, [sel, sel])
+        ctc = plan.cl_batch(rqs, bl.BLAST_BF16S, [sel, sel])
+        for rq, a, b in zip(rqs, c64, ctc):
+            Co = g.cl(To, g.fit(rq.k_tab, rq.p_tab), 1, 1, rq.kern_chi, rq.kern_Rchi, rq.growth_chi,
+                      rq.growth_Rchi, ell_subset=g.ells[sel])
+            assert a.shape == Co.shape == (3, 4)
+            assert np.max(eij(a, Co, 1, 1)) < 1e-10
+            assert np.max(eij(b, Co, 1, 1)) < 1e-4
+    finally:
+        plan.close()
+
