@@ -56,3 +56,20 @@ def test_plan_rejects_unsorted_ells():
     spec.ells = spec.ells * 0 + 1
     with pytest.raises(bl.BlastError):
         bl.Plan(spec)
+
+
+def test_server_entry_points_reject_bad_arguments_on_the_host():
+    L = bl.lib()
+    out = ctypes.c_void_p()
+    t = ctypes.c_uint64()
+    d = ctypes.c_int()
+    req = bl.blast_request()
+    # no plans, no budget, no slots, no output handle: refused before any device work
+    assert L.blast_server_create(None, 1, 1 << 20, 4, ctypes.byref(out)) == bl.BLAST_EINVAL
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.blast_server_create(arr, 1, 1 << 20, 4, ctypes.byref(out)) == bl.BLAST_EINVAL
+    assert L.blast_server_create(arr, 0, 1 << 20, 4, ctypes.byref(out)) == bl.BLAST_EINVAL
+    assert L.blast_submit(None, 0, ctypes.byref(req), bl.BLAST_FP64, ctypes.byref(t)) == bl.BLAST_EINVAL
+    assert L.blast_poll(None, 1, None, ctypes.byref(d), 0) == bl.BLAST_EINVAL
+    assert L.blast_server_destroy(None) == bl.BLAST_EINVAL
+    assert L.blast_cl_batch(None, 1, ctypes.byref(req), bl.BLAST_FP64, None, 0, None) == bl.BLAST_EINVAL
