@@ -86,7 +86,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -260,7 +260,7 @@ def run_blast(args):
     ms_main, prof_main = timed(prec_main, args.steps, args.warmup, profile=True)
     clocks = clk.stop()
     C_main = [o.cpu().numpy() for o in outs]
-    k64 = max(2, args.steps // 4)
+    k64 = max(2, min(20, args.steps // 4))  # FP64 steps: ~150 ms each at the benchmark batch
     ms_64, _ = timed(bl.BLAST_FP64, k64, 1)
     C_64 = [o.cpu().numpy() for o in outs]
     err = max(float(np.max(eij(a, b, 5, 5))) for a, b in zip(C_main, C_64))
@@ -443,7 +443,7 @@ def serve_latency(plan, rqs, prec, prec_name, rate, seconds, seed=2000):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--impl", default="blast", choices=["blast", "reference"])
