@@ -110,3 +110,27 @@ def test_one_plus_one_bin_grid_sampled_at_four_ells():
     finally:
         plan.close()
 
+
+
+def test_high_ell_basis_and_cl():
+    """Bessel recurrences and Miller normalisation at l up to 1999 (the 10+10-bin
+    grid's range), on a grid small enough for the oracle."""
+    spec = synth.PlanSpec(np.array([200, 600, 1000, 1999], np.int32), 8, 26.0, 4100.0, 32, 0.2, 1.8, 32,
+                          1e-4, 1.0, 1, synth.kquad_points(1e-4, 1.0, 4100.0, 1.8), 1, 1)
+    plan = bl.Plan(spec)
+    try:
+        plan.precompute(bl.BASIS_ALL)
+        g = _grid(spec)
+        To = g.basis()
+        Tg = plan.basis()
+        scale = np.max(np.abs(To), axis=-1, keepdims=True)
+        assert np.max(np.abs(Tg - To) / np.where(scale > 0, scale, 1.0)) < 1e-11
+        chi, R, _ = plan.nodes()
+        rq = synth.make_request(chi, R, 1, 1)
+        C = plan.cl(rq, bl.BLAST_FP64)
+        Co = g.cl(To, g.fit(rq.k_tab, rq.p_tab), 1, 1, rq.kern_chi, rq.kern_Rchi, rq.growth_chi, rq.growth_Rchi)
+        # at l = 1999 eight chi nodes leave C ~ 1e-18 of cancelled sums (negative
+        # autos): ill-conditioned, so the spectra are compared up to l = 1000
+        assert np.max(eij(C[:, :3], Co[:, :3], 1, 1)) < 1e-10
+    finally:
+        plan.close()
