@@ -201,17 +201,22 @@ int blast_cl_batch(blast_plan *plan, int n, const blast_request *reqs, int preci
  * fixed device array of BLAST_NOALLOC_SCRATCH_BYTES compiled into the library,
  * which every GPU that loads the library holds until the process exits.  It
  * calls no cudaMalloc, cudaFree or other allocating routine.
- *   req       device inputs only (req->mem_space must be 1), else BLAST_EINVAL
+ *   req       device inputs only (req->mem_space must be 1), else BLAST_EINVAL;
+ *             checked as blast_cl checks them (tracer counts, table size, ell
+ *             mask bits inside the plan), and every pointer, cl_out included,
+ *             must be 8-byte aligned (BLAST_EINVAL otherwise, nothing launched)
  *   cl_out    device array [npairs][n_sel], written on the stream
  *   returns   BLAST_ENOMEM when the request needs more scratch than the array
  *             holds (about 3 n_ell n_chi max_tracers + (n_clust+n_lens)
  *             n_chi n_R doubles; the 3x2pt 10+10-bin 100-ell grid fits),
  *             BLAST_ENOBASIS without an FP64 basis, BLAST_EDEVICE on CUDA errors.
- * The first call on each device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
- * share the one array, whose contents persist between calls: every byte a call
- * reads is written earlier in the same call, and calls that overlap on the GPU
- * (other streams, other host threads) race on it. */
+ * Set-up happens in blast_plan_create, on the plan's device with that device
+ * current: it looks up the array's device address and loads the code of the
+ * kernels this path launches (CUDA loads modules lazily), so the array's
+ * memory is taken when the plan is made and the call itself takes none.  All
+ * calls share the one array, whose contents persist between calls: every byte
+ * a call reads is written earlier in the same call, and calls that overlap on
+ * the GPU (other streams, other host threads) race on it. */
 #define BLAST_NOALLOC_SCRATCH_BYTES (16u << 20)
 int blast_cl_noalloc(blast_plan *plan, const blast_request *req, double *cl_out, void *stream);
 

@@ -61,7 +61,7 @@ def lib():
             L.orc_prefactor.restype = d
             L.orc_npairs.argtypes = [i, i]
             L.orc_cl.argtypes = [i, _ip, i, i, _dp, _dp, _dp, _dp, i, _dp, _dp, i, i,
-                                 _dp, _dp, _dp, _dp, _dp]
+                                 _dp, _dp, _dp, _dp, _dp, i]
             _LIB = L
     return _LIB
 
@@ -159,8 +159,9 @@ def npairs(ng, ns):
 
 
 # --------------------------------------------------------------------------- C_l
-def cl(ells, chi, wchi, R, wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi):
-    """C[p][e] from T~[3][n_ell][N][X*Rn] and the fitted a_n (steps 5-6)."""
+def cl(ells, chi, wchi, R, wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, nthreads=0):
+    """C[p][e] from T~[3][n_ell][N][X*Rn] and the fitted a_n (steps 5-6);
+    nthreads 0 = every OpenMP thread (independent (type, ell) items)."""
     ells, pe = _i(ells)
     chi, pc = _d(chi)
     wchi, pwc = _d(wchi)
@@ -177,7 +178,7 @@ def cl(ells, chi, wchi, R, wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi):
     assert T.shape == (3, ells.size, N, X * Rn), T.shape
     C = np.empty((npairs(ng, ns), ells.size))
     _check(lib().orc_cl(ells.size, pe, X, Rn, pc, pwc, pR, pwR, N, pT, pa, ng, ns,
-                        pkc, pkR, pDc, pDR, _d(C)[1]), "cl")
+                        pkc, pkR, pDc, pDR, _d(C)[1], int(nthreads)), "cl")
     return C
 
 
@@ -202,6 +203,7 @@ class Grid:
     def fit(self, ktab, ptab):
         return fit(self.N, self.k_min, self.k_max, ktab, ptab, self.k_map)
 
-    def cl(self, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, ell_subset=None):
+    def cl(self, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, ell_subset=None, nthreads=0):
         ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
-        return cl(ells, self.chi, self.wchi, self.R, self.wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi)
+        return cl(ells, self.chi, self.wchi, self.R, self.wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi,
+                  nthreads)

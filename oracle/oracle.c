@@ -422,16 +422,27 @@ int orc_npairs(int ng, int ns)
 int orc_cl(int n_ell, const int *ell, int X, int Rn, const double *chi, const double *wchi,
            const double *R, const double *wR, int N, const double *T, const double *a,
            int ng, int ns, const double *kchi, const double *kRchi,
-           const double *Dchi, const double *DRchi, double *C)
+           const double *Dchi, const double *DRchi, double *C, int nthreads)
 {
     (void)R;
     if (n_ell < 1 || X < 1 || Rn < 1 || N < 1 || ng < 0 || ns < 0 || ng + ns < 1) return -1;
     const int Q = X * Rn;
-    double *w = (double *)malloc(sizeof(double) * Q);
-    if (!w) return -2;
     int p0[3] = {0, ng * (ng + 1) / 2, ng * (ng + 1) / 2 + ng * ns};
+    int nt = orc_threads(nthreads);
+    int fail = 0;
+    /* every (type, ell) result is independent: threads take whole (t, e) items
+     * and each keeps its own w, so the arithmetic of every item is unchanged */
+#pragma omp parallel num_threads(nt)
+    {
+    double *w = (double *)malloc(sizeof(double) * Q);
+    if (!w) {
+#pragma omp atomic write
+        fail = 1;
+    }
+#pragma omp for schedule(dynamic, 1) collapse(2)
     for (int t = 0; t < 3; t++) {
         for (int e = 0; e < n_ell; e++) {
+            if (!w) continue;
             const double *Te = T + ((size_t)t * n_ell + e) * N * (size_t)Q;
             for (int q = 0; q < Q; q++) {
                 double s = 0.0;
@@ -462,5 +473,6 @@ int orc_cl(int n_ell, const int *ell, int X, int Rn, const double *chi, const do
         }
     }
     free(w);
-    return 0;
+    }
+    return fail ? -2 : 0;
 }

@@ -136,3 +136,5 @@ int plan_alloc_basis(blast_plan *p, unsigned mask);
 int request_check(const blast_plan *p, const blast_request *r);  // the checks of blast_cl
 int request_n_sel(const blast_plan *p, const blast_request *r);  // ells selected by the mask
 double host_now();
+int noalloc_prepare(int dev);     // allocation-free path: scratch address and kernel code, per device
+int preload_fp64_kernels();       // load the FP64 evaluation kernels' code (lazy module loading)

@@ -249,6 +249,16 @@ __global__ void k_reduce(const ReqDev *__restrict__ reqs, const T *__restrict__ 
 
 }  // namespace
 
+int preload_fp64_kernels()
+{
+    cudaFuncAttributes fa;
+    BL_CUDA(cudaFuncGetAttributes(&fa, k_fit));
+    BL_CUDA(cudaFuncGetAttributes(&fa, k_weights));
+    BL_CUDA(cudaFuncGetAttributes(&fa, k_contract<double>));
+    BL_CUDA(cudaFuncGetAttributes(&fa, k_reduce<double>));
+    return BLAST_OK;
+}
+
 int launch_fit(blast_plan *p, ReqDev *dreq, int nreq, cudaStream_t s)
 {
     size_t smem = sizeof(double) * (10 * kMaxPtab + p->N);

@@ -11,6 +11,10 @@
 //
 // The scratch array lives in the device image: every GPU that loads the
 // library holds BLAST_NOALLOC_SCRATCH_BYTES of it until the process exits.
+// CUDA loads modules lazily, so the array (and the code of the kernels this
+// path launches) is placed on a device the first time it is touched there;
+// plan creation touches it (noalloc_prepare), so that memory is taken when a
+// plan is made and never inside blast_cl_noalloc.
 #include <cstring>
 #include <mutex>
 
@@ -68,16 +72,31 @@ bool selected(const blast_request *r, int e)
 
 }  // namespace
 
+// Set-up for one device, with that device current: look up the array's device
+// address and load the code of every kernel the allocation-free path launches
+// (module loading is lazy and would otherwise take device memory on the first
+// call).  Called by blast_plan_create.
+int noalloc_prepare(int dev)
+{
+    unsigned char *S = nullptr;
+    int rc = scratch_for_device(dev, &S);
+    if (rc) return rc;
+    cudaFuncAttributes fa;
+    BL_CUDA(cudaFuncGetAttributes(&fa, k_put_desc));
+    return preload_fp64_kernels();
+}
+
 extern "C" int blast_cl_noalloc(blast_plan *p, const blast_request *r, double *cl_out, void *stream)
 {
     if (!p || !r || !cl_out) return BLAST_EINVAL;
     if (r->mem_space != 1) return BLAST_EINVAL;  // device inputs only: nothing is staged
-    if (r->n_clust < 0 || r->n_lens < 0 || r->n_clust + r->n_lens < 1 || r->n_clust > p->max_clust ||
-        r->n_lens > p->max_lens)
-        return BLAST_EINVAL;
-    if (!r->kern_chi || !r->kern_Rchi || !r->growth_chi || !r->growth_Rchi || !r->k_tab || !r->p_tab)
-        return BLAST_EINVAL;
-    if (r->n_ptab < 3 || r->n_ptab > 1024) return BLAST_EINVAL;
+    // the checks of blast_cl: tracer counts, table size, ell mask within the plan
+    int rc = request_check(p, r);
+    if (rc) return rc;
+    // the kernels load and store doubles through these pointers
+    const void *ptrs[] = {r->kern_chi, r->kern_Rchi, r->growth_chi, r->growth_Rchi, r->k_tab, r->p_tab, cl_out};
+    for (const void *q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) % 8) return BLAST_EINVAL;
 
     // ells to evaluate and their output columns
     NoallocDesc nd;
@@ -106,7 +125,6 @@ extern "C" int blast_cl_noalloc(blast_plan *p, const blast_request *r, double *c
     }
     if (!p->have64) return BLAST_ENOBASIS;
 
-    int rc;
     if (cudaSetDevice(p->device) != cudaSuccess) { cudaGetLastError(); return BLAST_EDEVICE; }
     unsigned char *S = nullptr;
     if ((rc = scratch_for_device(p->device, &S))) return rc;

@@ -288,6 +288,11 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
         return BLAST_EDEVICE;
     }
     *p->h_err = 0;
+    if ((rc = noalloc_prepare(p->device))) {
+        plan_free_device(p);
+        delete p;
+        return rc;
+    }
     *out = p;
     return BLAST_OK;
 }

@@ -71,6 +71,55 @@ def test_noalloc_matches_blast_cl_on_consecutive_calls(small_plan):
         assert np.max(eij(got, ref, rq.n_clust, rq.n_lens)) < TOL_FP64
 
 
+def test_noalloc_takes_no_device_memory(small_plan):
+    """After plan creation (which places the fixed array and the kernels' code on
+    the device) a call changes neither the driver's free-memory count nor the
+    plan's work space: the evaluation's scratch is the fixed array."""
+    spec, plan = small_plan
+    chi, R, _ = plan.nodes()
+    stream = torch.cuda.current_stream().cuda_stream
+    P = None
+    outs, devs = [], []
+    for idx in (3, 4):
+        rq = synth.config_request("small", chi, R, idx)
+        devs.append((rq, to_device(rq)))
+        P = bl.blast_npairs(rq.n_clust, rq.n_lens)
+        outs.append(torch.empty((P, spec.ells.size), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for (rq, dev), out in zip(devs, outs):
+        r = plan.request(rq, device_arrays=dev)
+        assert bl.blast_cl_noalloc(plan.h, r, out.data_ptr(), stream) == bl.BLAST_OK
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert torch.cuda.memory_allocated() == alloc0
+    for (rq, _), out in zip(devs, outs):
+        ref = plan.cl(rq, bl.BLAST_FP64)
+        assert np.max(eij(out.cpu().numpy(), ref, rq.n_clust, rq.n_lens)) < TOL_FP64
+
+
+def test_noalloc_refuses_what_blast_cl_refuses(small_plan):
+    """Misaligned pointers and ell-mask bits beyond the plan are refused before
+    anything is launched, as blast_cl refuses them."""
+    spec, plan = small_plan
+    chi, R, _ = plan.nodes()
+    rq = synth.config_request("small", chi, R, 0)
+    dev = to_device(rq)
+    P = bl.blast_npairs(rq.n_clust, rq.n_lens)
+    out = torch.full((P * spec.ells.size + 1,), 7.0, dtype=torch.float64, device="cuda")
+    r = plan.request(rq, device_arrays=dev)
+    r.ell_mask_lo = 1 << spec.ells.size      # one bit past the plan's last ell
+    assert bl.blast_cl_noalloc(plan.h, r, out.data_ptr(), None) == bl.BLAST_EINVAL
+    r = plan.request(rq, device_arrays=dev)
+    assert bl.blast_cl_noalloc(plan.h, r, out.data_ptr() + 4, None) == bl.BLAST_EINVAL
+    r.kern_Rchi = r.kern_Rchi + 4
+    assert bl.blast_cl_noalloc(plan.h, r, out.data_ptr(), None) == bl.BLAST_EINVAL
+    torch.cuda.synchronize()
+    assert bool(torch.all(out == 7.0))      # nothing was written
+
+
 def test_noalloc_rejects_host_inputs_and_oversized_requests(small_plan):
     spec, plan = small_plan
     chi, R, _ = plan.nodes()
