@@ -122,54 +122,111 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- oracle (CPU) timing
-def oracle_sample(n_req=4, ell_stride=4, seed=7):
-    """Time the FP64 oracle's per-cosmology evaluation (fit + contraction +
-    quadrature; the basis is excluded as in the paper) on the benchmark grid
-    for a subset of ells.  The oracle's basis for this grid would take hours
-    to build on the host, and its evaluation loops cost the same whatever the
-    basis values are, so the sample feeds it a seeded random basis of the
-    right shape.  Returns (C_l-sets/s, seconds, description, threads)."""
-    import oracle
-    from paper_2410_03632_gb300 import synth
-    spec = synth.plan_spec("c1")
-    g = oracle.Grid(spec.ells, spec.n_chi, spec.chi_min, spec.chi_max, spec.n_R, spec.R_min, spec.R_max,
-                    spec.n_cheb, spec.k_min, spec.k_max, spec.n_kquad, spec.k_map)
-    sub = spec.ells[::ell_stride]
-    rng = np.random.default_rng(seed)
-    T = rng.standard_normal((3, sub.size, spec.n_cheb, spec.n_chi * spec.n_R))
-    rqs = [synth.config_request("c1", g.chi, g.R, 1 + i) for i in range(n_req)]
-    t0 = time.perf_counter()
-    for rq in rqs:
-        a = g.fit(rq.k_tab, rq.p_tab)
-        g.cl(T, a, rq.n_clust, rq.n_lens, rq.kern_chi, rq.kern_Rchi, rq.growth_chi, rq.growth_Rchi,
-             ell_subset=sub)
-    dt = time.perf_counter() - t0
-    sets = n_req * sub.size / spec.ells.size
-    desc = (f"{n_req} cosmologies x {sub.size} of 64 ells (every {ell_stride}th) on the benchmark grid, "
-            f"oracle fit + contraction + quadrature, seeded random basis of the right shape; "
-            f"scaled to full C_l-sets")
-    return sets / dt, dt, desc, 1
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+class OracleSample:
+    """The FP64 oracle's per-cosmology evaluation (fit + contraction +
+    quadrature; the basis is excluded as in the paper) on the benchmark grid,
+    for a subset of ells.  The oracle's basis for this grid would take hours to
+    build on the host, and its evaluation loops cost the same whatever the
+    basis values are, so the sample feeds it a seeded random basis of the right
+    shape."""
+
+    def __init__(self, n_req=4, ell_stride=4, seed=7):
+        import oracle
+        from paper_2410_03632_gb300 import synth
+        spec = synth.plan_spec("c1")
+        self.g = oracle.Grid(spec.ells, spec.n_chi, spec.chi_min, spec.chi_max, spec.n_R, spec.R_min,
+                             spec.R_max, spec.n_cheb, spec.k_min, spec.k_max, spec.n_kquad, spec.k_map)
+        self.sub = spec.ells[::ell_stride]
+        rng = np.random.default_rng(seed)
+        self.T = rng.standard_normal((3, self.sub.size, spec.n_cheb, spec.n_chi * spec.n_R))
+        self.rqs = [synth.config_request("c1", self.g.chi, self.g.R, 1 + i) for i in range(n_req)]
+        self.sets = n_req * self.sub.size / spec.ells.size   # C_l-sets one run evaluates
+        self.desc = (f"{n_req} cosmologies x {self.sub.size} of {spec.ells.size} ells (every {ell_stride}th) "
+                     f"on the benchmark grid, oracle fit + contraction + quadrature, seeded random basis "
+                     f"of the right shape; scaled to full C_l-sets")
+
+    def run(self, threads):
+        """Seconds for one pass over the sample with `threads` OpenMP threads."""
+        t0 = time.perf_counter()
+        for rq in self.rqs:
+            a = self.g.fit(rq.k_tab, rq.p_tab)
+            self.g.cl(self.T, a, rq.n_clust, rq.n_lens, rq.kern_chi, rq.kern_Rchi, rq.growth_chi,
+                      rq.growth_Rchi, ell_subset=self.sub, nthreads=threads)
+        return time.perf_counter() - t0
+
+
+def cpu_baseline(reps=10):
+    """Oracle throughput on the host cores at 1 thread and at every core: the
+    median of `reps` passes after one warm-up pass, in C_l-sets/s."""
+    smp = OracleSample()
+    cores = os.cpu_count() or 1
+    res = {}
+    for th in (1, cores):
+        smp.run(th)
+        ts = [smp.run(th) for _ in range(reps)]
+        res[th] = (smp.sets / statistics.median(ts), sum(ts))
+    return {"value": res[cores][0], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1_thread": res[1][0], "nproc": cores, "cpu_model": cpu_model(),
+            "statistic": f"median of {reps} passes after 1 warm-up, per thread count",
+            "seconds": res[1][1] + res[cores][1], "sample": smp.desc}
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: each step is one pass over a
+    bounded sample (one cosmology, 16 of the 64 ells), scaled to C_l-sets."""
     rank, _, world = env_rank()
     if rank != 0:
         return
+    smp = OracleSample(n_req=1)
+    cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle_sample(n_req=1)
-    vals, secs = [], 0.0
-    for _ in range(args.steps):
-        v, dt, desc, cores = oracle_sample(n_req=1)
-        vals.append(v)
-        secs += dt
-    value = args.steps * (1 * 16 / 64) / secs
+        smp.run(cores)
+    secs = sum(smp.run(cores) for _ in range(args.steps))
+    value = args.steps * smp.sets / secs
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args.batch, world),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu_model": cpu_model(), "sample": smp.desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def alu_peaks():
+    """CUDA-core FMA peaks (TFLOP/s) measured by the probe library's own kernels:
+    FP64, FP32 scalar and FP32 packed pairs."""
+    import ctypes
+    from paper_2410_03632_gb300 import build as _b
+    L = ctypes.CDLL(_b.build_probe())
+    L.peak_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for kind, name, iters in ((0, "fp64_tflops", 8000), (1, "fp32_tflops", 200000), (2, "fp32x2_tflops", 100000)):
+        tf, ms = ctypes.c_double(), ctypes.c_double()
+        if L.peak_probe(kind, iters, ctypes.byref(tf), ctypes.byref(ms)) == 0:
+            out[name] = tf.value
+    out["how"] = ("own kernels: 8 independent dependent-FMA chains per thread, 8 blocks of 256 threads "
+                  "per SM, one timed launch after a warm-up (CUDA events)")
+    return out
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -261,7 +318,7 @@ def run_blast(args):
     clocks = clk.stop()
     C_main = [o.cpu().numpy() for o in outs]
     k64 = max(2, min(20, args.steps // 4))  # FP64 steps: ~150 ms each at the benchmark batch
-    ms_64, _ = timed(bl.BLAST_FP64, k64, 1)
+    ms_64, prof_64 = timed(bl.BLAST_FP64, k64, 1, profile=True)
     C_64 = [o.cpu().numpy() for o in outs]
     err = max(float(np.max(eij(a, b, 5, 5))) for a, b in zip(C_main, C_64))
 
@@ -272,14 +329,23 @@ def run_blast(args):
     L, N, Q, X = plan.L, plan.N, plan.Q, plan.X
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    method_flops = 2.0 * 3 * L * N * Q * B          # contraction (a), one multiply-add per product
     if have_tc:
-        # 15 BF16 slice products per coefficient-basis product, K padded to 64
-        flops = 2.0 * 3 * L * 64 * Q * (-(-B // 128) * 128) * 15
-        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        # the roofline flops: the method's products with the split-MMA allowance x3;
+        # the kernel is timed alone in its launch, so the burst BF16 peak applies
+        flops = method_flops * 3
+        peak = peaks.get("bf16_tflops", 1900.0)
         achieved = flops / (avg_ms * 1e-3) / 1e12
+        # what the tensor cores actually execute: 15 BF16 slice products per
+        # product, K padded to the swizzle row, cosmologies padded to the tile
+        slice_flops = 2.0 * 3 * L * (-(-N // 64) * 64) * Q * (-(-B // 128) * 128) * 15
+        slice_rate = slice_flops / (avg_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "peak_kind": "bf16 sustained, of measured",
-                "traffic": traffic_for("contract_tc.cu", "contract_tc")}
+                "frac": achieved / peak, "peak_kind": "bf16 burst, of measured",
+                "flops_per_launch": flops, "flops_def": "2*3*L*N*Q*B x3 (split-MMA allowance)",
+                "traffic": traffic_for("contract_tc.cu", "contract_tc"),
+                "slice_mma": {"achieved": slice_rate, "frac": slice_rate / peak, "flops_per_launch": slice_flops,
+                              "def": "15 BF16 slice products per product, K padded to 64, M padded to 128"}}
     else:
         ntr = 10
         alg_bytes = 3 * L * N * Q * 4 + B * (ntr * Q * 4 + N * 4 + 3 * L * X * 5 * 4)
@@ -290,6 +356,24 @@ def run_blast(args):
     roof["kernel"] = kname
     roof["avg_launch_ms"] = avg_ms
     roof["launches"] = klaunch
+    # the other kernels against their own bounds
+    alu = alu_peaks()
+    kern = {}
+    rms, rl = prof_main["reduce"]
+    if rl and have_tc:
+        ntr_max = plan.max_clust + plan.max_lens
+        red_bytes = (B * 3 * L * X * (plan.Rn // 32) * 5 * 8 + ntr_max * X * (-(-B // 128) * 128) * 8
+                     + B * P * L * 8)
+        gbs = red_bytes / (rms / rl * 1e-3) / 1e9
+        kern["reduce"] = {"bound": "hbm", "bytes_per_launch": red_bytes, "achieved": gbs,
+                          "peak": peaks.get("hbm_gbs"), "frac": gbs / peaks.get("hbm_gbs", 6800.0),
+                          "unit": "GB/s"}
+    cms, cl64 = prof_64["contract"]
+    if cl64:
+        tf = method_flops / (cms / cl64 * 1e-3) / 1e12
+        kern["contract_fp64"] = {"bound": "alu", "achieved": tf, "peak": alu.get("fp64_tflops"),
+                                 "frac": tf / alu["fp64_tflops"] if alu.get("fp64_tflops") else None,
+                                 "unit": "TFLOP/s", "peak_kind": "FP64 FMA, measured by the probe kernels"}
 
     # single-request latency (p50 / p99) of the mixed path
     # the comparator of the serving numbers: requests one at a time in FP64
@@ -363,6 +447,8 @@ def run_blast(args):
                                "req_per_s": 1e3 * len(lat) / sum(lat),
                                "what": "one blast_cl call per cosmology, FP64 path, device inputs, back to back"},
         "roofline": roof,
+        "kernel_bounds": kern,
+        "alu_peaks": alu,
         "e2e": {"value": job_throughput(world, B, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -371,9 +457,7 @@ def run_blast(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, desc, cores = oracle_sample()
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
-                                "seconds": dt}
+        line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

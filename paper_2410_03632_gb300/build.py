@@ -18,8 +18,12 @@ OUT_DIR = os.path.join(HERE, "_lib")
 SO = os.path.join(OUT_DIR, "libblast.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+# Host code (the plan's quadrature nodes) is compiled without fused multiply-add
+# contraction, so every node is the plain IEEE evaluation of its formula on any
+# host: the basis integrand oscillates as j_l(k chi) with k chi up to ~1e5, so a
+# node one ulp off shifts its phase by ~1e-11.
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", INC]
+         "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", INC]
 
 
 def _sources():
@@ -37,7 +41,28 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
+PROBE_SRC = os.path.join(HERE, "probe", "peaks.cu")
+PROBE_SO = os.path.join(OUT_DIR, "libpeaks.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """The CUDA-core FMA peak microbenchmark (a separate library the benchmark
+    loads to state ALU roofline denominators)."""
+    if not force and os.path.exists(PROBE_SO) and os.path.getmtime(PROBE_SO) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_SO
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PROBE_SO + f".tmp{os.getpid()}"
+    cmd = [NVCC] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PROBE_SRC, "-o", tmp,
+                           "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_SO)
+    return PROBE_SO
+
+
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+    build_probe(force)
     if not force and up_to_date():
         return SO
     os.makedirs(OUT_DIR, exist_ok=True)

@@ -224,6 +224,13 @@ def plan_spec(name: str) -> PlanSpec:
         # few ells and chi nodes with k_max = 1, so the oracle's basis takes seconds
         return PlanSpec(np.array([2, 30, 120, 300], np.int32), 24, 26.0, 4100.0, 192, 0.2, 1.8, 96, 1e-4, 1.0, 1,
                         kquad_points(1e-4, 1.0, 4100.0, 1.8), 10, 10)
+    elif name == "c1hi":
+        # the 3x2pt grid's k range (to 10 h/Mpc), order 64, bins and chi range on
+        # nine chi nodes, n_R = 64 and four ells to 1000: high-l lensing spectra of
+        # the z = 0.2 bin, where the Chebyshev sum cancels hardest, at a size the
+        # oracle's basis finishes in about a minute
+        return PlanSpec(np.array([2, 300, 600, 1000], np.int32), 9, 26.0, 4100.0, 64, 0.2, 1.8, 64,
+                        1e-4, 10.0, 1, kquad_points(1e-4, 10.0, 4100.0, 1.8), 5, 5)
     elif name == "tc":
         # tensor-core path shapes: n_R a multiple of 32, n_cheb <= 64, <= 5 tracers per kind
         return PlanSpec(ell_list(9, 2, 300), 21, 40.0, 2400.0, 64, 0.2, 1.8, 40, 1e-4, 1.0, 1,
@@ -237,7 +244,7 @@ def plan_spec(name: str) -> PlanSpec:
 def config_request(name: str, chi, R, idx: int = 0) -> Request:
     """The seeded request of a workload: seed 1000 + config + 7919 idx."""
     spec = plan_spec(name)
-    cfg = {"c0": 0, "c1": 1, "c2": 2, "tiny": 10, "small": 11, "tc": 12, "c2s": 13}[name]
+    cfg = {"c0": 0, "c1": 1, "c2": 2, "tiny": 10, "small": 11, "tc": 12, "c2s": 13, "c1hi": 1}[name]
     rng = np.random.default_rng(1000 + cfg + 7919 * idx)
     ng, ns = spec.max_clust, spec.max_lens
     zb = {}

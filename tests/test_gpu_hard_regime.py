@@ -1,0 +1,122 @@
+"""Parity where the Chebyshev sum of Eq. pmd cancels hardest.
+
+Grid: the 3x2pt workload's k range (1e-4..10 h/Mpc, log map, 65 537 k nodes),
+Chebyshev order 64, its 5 + 5 bins (means 0.2..1.5) and chi range to 4100
+Mpc/h, on nine chi nodes, n_R = 64 and the ells 2, 300, 600 and 1000.  At
+high l the basis of the low-z lensing spectra probes k of a few h/Mpc, where
+P(k) is about 1e-6 of its Chebyshev coefficients, so sum_n a_n T~_n cancels by
+about that factor (Sec. 3.1: the expansion of Eq. cheb_pk reaches small P only
+through cancellation).  The FP32 CUDA-core path fails here by design; the test
+checks that it does, so the regime is the hard one.
+
+Two comparisons, element by element over every spectrum and ell:
+  P1  the library fed the oracle's basis (blast_basis_set): FP64 and the
+      allocation-free FP64 entry point within e_ij <= 1e-10, the tcgen05
+      five-slice path within 1e-4 of the oracle's C_l;
+  P3  the library with its own device-computed basis, end to end: the
+      five-slice path within 1e-4; FP64 within the bar that the two bases'
+      agreement allows (stated below).
+e_ij = |dC_ij| / sqrt(C_ii C_jj) (auto-spectrum normalisation).
+"""
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2410_03632_gb300 import blast as bl
+from paper_2410_03632_gb300 import synth
+from tests.metrics import eij, pair_list
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch_cuda():
+    try:
+        import torch
+        return torch if torch.cuda.is_available() else None
+    except Exception:
+        return None
+
+
+torch = _torch_cuda()
+if torch is None:
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+FIELDS = ["kern_chi", "kern_Rchi", "growth_chi", "growth_Rchi", "k_tab", "p_tab"]
+N_COSMO = 4
+
+
+def worst_by_type(e, ng, ns, ells):
+    """{(pair type, ell): worst e_ij} over the pairs of each type."""
+    types = np.array([t for t, _, _ in pair_list(ng, ns)])
+    return {(t, int(l)): float(np.max(e[types == t, k])) for t in range(3) for k, l in enumerate(ells)}
+
+
+@pytest.fixture(scope="module")
+def hard():
+    spec = synth.plan_spec("c1hi")
+    g = orc.Grid(spec.ells, spec.n_chi, spec.chi_min, spec.chi_max, spec.n_R, spec.R_min, spec.R_max,
+                 spec.n_cheb, spec.k_min, spec.k_max, spec.n_kquad, spec.k_map)
+    To = g.basis()
+    plan_o = bl.Plan(spec)
+    plan_o.set_basis(To, bl.BASIS_ALL)
+    plan_g = bl.Plan(spec)
+    plan_g.precompute(bl.BASIS_ALL)
+    chi, R, _ = plan_o.nodes()
+    assert np.allclose(chi, g.chi, rtol=1e-15) and np.allclose(R, g.R, rtol=1e-15)
+    rqs = [synth.config_request("c1hi", chi, R, i) for i in range(N_COSMO)]
+    Co = [g.cl(To, g.fit(rq.k_tab, rq.p_tab), rq.n_clust, rq.n_lens, rq.kern_chi, rq.kern_Rchi,
+               rq.growth_chi, rq.growth_Rchi) for rq in rqs]
+    yield spec, g, To, plan_o, plan_g, rqs, Co
+    plan_o.close()
+    plan_g.close()
+
+
+def test_regime_is_hard(hard):
+    """Plain FP32 loses the cancellation: its worst e_ij is far above 1e-4."""
+    spec, g, To, plan_o, plan_g, rqs, Co = hard
+    worst = max(float(np.max(eij(C, o, 5, 5))) for C, o in zip(plan_o.cl_batch(rqs, bl.BLAST_FP32), Co))
+    print(f"\nFP32 CUDA-core path, oracle basis: worst e_ij {worst:.3e}")
+    assert worst > 1e-3
+
+
+def test_p1_oracle_basis(hard):
+    spec, g, To, plan_o, plan_g, rqs, Co = hard
+    c64 = plan_o.cl_batch(rqs, bl.BLAST_FP64)
+    ctc = plan_o.cl_batch(rqs, bl.BLAST_BF16S)
+    stream = torch.cuda.current_stream().cuda_stream
+    w64 = wtc = wna = 0.0
+    table = {}
+    for rq, a, b, o in zip(rqs, c64, ctc, Co):
+        dev = {f: torch.from_numpy(np.ascontiguousarray(getattr(rq, f))).cuda() for f in FIELDS}
+        out = torch.empty(o.shape, dtype=torch.float64, device="cuda")
+        assert bl.blast_cl_noalloc(plan_o.h, plan_o.request(rq, device_arrays=dev), out.data_ptr(),
+                                   stream) == bl.BLAST_OK
+        torch.cuda.synchronize()
+        e_tc = eij(b, o, 5, 5)
+        w64 = max(w64, float(np.max(eij(a, o, 5, 5))))
+        wtc = max(wtc, float(np.max(e_tc)))
+        wna = max(wna, float(np.max(eij(out.cpu().numpy(), o, 5, 5))))
+        for k, v in worst_by_type(e_tc, 5, 5, spec.ells).items():
+            table[k] = max(table.get(k, 0.0), v)
+    print(f"\nP1 (oracle basis): FP64 {w64:.3e}  no-alloc FP64 {wna:.3e}  BF16 five-slice {wtc:.3e}")
+    for (t, l), v in sorted(table.items()):
+        print(f"  five-slice worst e_ij  type {'gg gs ss'.split()[t]}  l = {l:5d}: {v:.3e}")
+    assert w64 < 1e-10
+    assert wna < 1e-10
+    assert wtc < 1e-4
+
+
+def test_p3_device_basis(hard):
+    spec, g, To, plan_o, plan_g, rqs, Co = hard
+    Tg = plan_g.basis()
+    scale = np.max(np.abs(To), axis=-1, keepdims=True)
+    db = float(np.max(np.abs(Tg - To) / np.where(scale > 0, scale, 1.0)))
+    c64 = plan_g.cl_batch(rqs, bl.BLAST_FP64)
+    ctc = plan_g.cl_batch(rqs, bl.BLAST_BF16S)
+    w64 = max(float(np.max(eij(a, o, 5, 5))) for a, o in zip(c64, Co))
+    wtc = max(float(np.max(eij(b, o, 5, 5))) for b, o in zip(ctc, Co))
+    print(f"\nP3 (device basis): basis vs oracle {db:.3e} of row max; FP64 C_l {w64:.3e}; "
+          f"BF16 five-slice {wtc:.3e}")
+    assert db < 1e-10
+    assert wtc < 1e-4
+    assert w64 < 1e-6
