@@ -185,8 +185,8 @@ int blast_cl(blast_plan *plan, const blast_request *req, int precision,
  * receives request i's C (layout as blast_cl).  BLAST_BF16S runs contraction
  * (a) as one tcgen05 GEMM over the batch (cosmologies x Chebyshev order x
  * chi-R nodes) with the R sum of quadrature (b) fused in its epilogue; it
- * needs n_R a multiple of 32, n_cheb <= 64 and at most 5 tracers of each kind
- * (BLAST_EINVAL otherwise). */
+ * needs n_R a multiple of 32, n_cheb <= 96 and at most 10 tracers of each
+ * kind (BLAST_EINVAL otherwise). */
 int blast_cl_batch(blast_plan *plan, int n, const blast_request *reqs, int precision,
                    double *const *outs, int out_mem_space, void *stream);
 

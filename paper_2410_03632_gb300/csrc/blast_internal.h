@@ -67,9 +67,10 @@ struct blast_plan {
     // basis tables
     double *T64 = nullptr;          // [3][L][N][Q]
     float *T32 = nullptr;           // [3][L][N][Q]
-    uint16_t *Tsl = nullptr;        // [S][3 L Q][Kp] bf16 slices (integer x 2^-8p), K-major (n fastest)
-    float *scT = nullptr;           // [3 L Q] 2^(eT - 16) per column
-    int Kp = 0;                     // N rounded up to a multiple of 64 (zero padded)
+    uint16_t *Tsl = nullptr;        // [S][3 L Q][Kst] bf16 slices (integer x 2^-8p), K-major (n fastest)
+    float *scT = nullptr;           // [3 L Q / 32] 2^(eG - 16) per 32-column tile
+    int Kmma = 0;                   // N rounded up to a multiple of 16 (the MMA's K)
+    int Kst = 0;                    // stored K of the slice table: max(64, Kmma), zero padded
     bool have64 = false, have32 = false, havebf = false;
     int *d_err = nullptr;           // host-mapped error word written by bounded device waits
     int *h_err = nullptr;
@@ -130,6 +131,7 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int nreq, const int *d_esel, i
                      const void *ypart, cudaStream_t s);
 int launch_basis_slices(blast_plan *p, cudaStream_t s);
 bool tc_supported(const blast_plan *p);
+size_t tc_y_bytes(const blast_plan *p, int n, int n_esel);  // R-tile partials of a tensor-core call
 
 // Host helpers
 int plan_alloc_basis(blast_plan *p, unsigned mask);

@@ -5,8 +5,8 @@
 //   Y_b(t, l, a, rt, j) = sum_{r in R-tile rt} V_bj(a, r) w_b(t, l, a n_R + r)
 //
 // as one GEMM per (t, l): M = cosmologies (128 per CTA, TMEM lanes), N = 32
-// chi-R nodes (one R-tile), K = Chebyshev order.  The expansion of P in
-// Chebyshev polynomials cancels strongly where P is small (high l, low-z
+// chi-R nodes (one R-tile), K = Chebyshev order (<= 96).  The expansion of P
+// in Chebyshev polynomials cancels strongly where P is small (high l, low-z
 // lensing), so an FP32-accumulated hi/lo split is not accurate enough.
 // Instead both operands are cut into S = 5 fixed-point slices of 8 bits:
 //
@@ -16,22 +16,29 @@
 // Slice p is stored as A_p 2^(-8p) (T_q 2^(-8q)): an integer of at most 9
 // bits times a power of two, exact in BF16.  Every product is exact, and level
 // k, D_k 2^(-8k) = sum_{p+q=k} sum_n (A_p 2^-8p)(T_q 2^-8q), is a multiple of
-// 2^(-8k) below 2^(23-8k) in magnitude, so the FP32 tensor-core accumulation
-// is exact.  The 15 slice pairs p+q <= 4 feed 5 level accumulators in TMEM;
-// the epilogue adds the levels with a cascade of fast two-sums, each exact for
-// operands on these grids, W 2^-32 = m + (e1 + e2 + e3 + e4), and scales by
-// 2^(ea + eT - 16).  The R sum that follows also cancels (w oscillates around
-// R = 1), so it runs on unevaluated pairs: exact products (FMA), two products
-// (columns two R nodes apart) added plainly, and two-sum accumulation of those
-// sums, two columns at a time in packed FP32 pairs; the pairs reach the chi
-// sum intact.
+// 2^(-8k) below 2^(24-8k) in magnitude for K <= 96, so the FP32 tensor-core
+// accumulation of levels 0, 1 and 2 is exact.  The 15 slice pairs p+q <= 4
+// feed LV accumulators in TMEM: five levels when K <= 64, else four, the last
+// holding levels 3 and 4 together (their sum lies 2^-24 below the leading
+// level; its FP32 rounding, about 2^-23 of that sum per MMA, is far below the
+// 2^-40 truncation of the slices).  The epilogue combines the levels with two
+// exact fast two-sums and one plain sum of the small parts,
+//   W 2^-32 = m + lo,   m = fl(fl(D_0 + D_1) + D_2),   lo = (e_1 + e_2) + (D_3 + D_4),
+// and scales by 2^(ea + eT - 16).  The R sum that follows also cancels (w
+// oscillates around R = 1), so it runs on unevaluated pairs: exact products
+// (FMA), two products (columns two R nodes apart) added plainly, and two-sum
+// accumulation of those sums, two columns at a time in packed FP32 pairs; the
+// pairs reach the chi sum intact.
 //
-// Warp roles (576 threads): warp 0 issues TMA loads of the basis slices,
-// warp 1 owns TMEM and issues tcgen05.mma (A = coefficient slices resident in
-// TMEM, B = basis slices in shared memory), warps 2..17 run the epilogue (one
-// TMEM lane = one cosmology per thread, four warps per lane quadrant, joined
-// by a named barrier per quadrant).  Every mbarrier wait is bounded; on
-// timeout the kernel records an error code in host-mapped memory and exits.
+// Warp roles (320 threads): warp 0 issues TMA loads of the basis slices into
+// a ring of stages, warp 1 owns TMEM and issues tcgen05.mma (A = coefficient
+// slices resident in TMEM, B = basis slices in shared memory) into two
+// accumulator buffers, warps 2..9 run the epilogue (one TMEM lane = one
+// cosmology per thread, two warps per lane quadrant with 16 columns each,
+// quadrature weights of up to five tracers per kind in registers, five more
+// in shared memory, the two column halves joined by a named barrier).  Every
+// mbarrier wait is bounded; on timeout the kernel records an error code in
+// host-mapped memory and exits after its copies and MMAs in flight complete.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -46,19 +53,30 @@ namespace {
 constexpr int kS = BLAST_TC_SLICES;       // slices per operand
 constexpr int kQT = 32;                   // chi-R nodes per tile (MMA N)
 constexpr int kM = 128;                   // cosmologies per tile (MMA M)
-constexpr int kKC = 64;                   // K elements per 128-byte swizzle row
-constexpr int kStages = 4;
-constexpr int kEP = 4;                    // epilogue warps per TMEM lane quadrant
-constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 16 epilogue warps
-constexpr int kHC = 32 / kEP;             // columns per epilogue thread
-constexpr int kNB = 5;                    // B-side tracers handled per thread (registers)
-constexpr uint32_t kACol = 2 * kS * kQT;          // TMEM column of the coefficient slices
-constexpr uint32_t kBSliceBytes = kQT * 128;      // 32 rows x 64 bf16
-constexpr uint32_t kBStageBytes = kS * kBSliceBytes;
+constexpr int kKC = 64;                   // K elements per 128-byte swizzle row (one TMA box)
+constexpr int kEP = 2;                    // epilogue warps per TMEM lane quadrant
+constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 8 epilogue warps
+constexpr int kHC = kQT / kEP;            // columns per epilogue thread
+constexpr int kCS = 4;                    // columns per TMEM load step
+constexpr int kNB = 5;                    // tracers per weight group
+constexpr int kNBUF = 2;                  // TMEM accumulator buffers
+constexpr uint32_t kBSliceBytes = kQT * 128;  // 32 rows x 64 bf16
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kCtrlBytes = 256;               // mbarriers, TMEM address, abort flag
+constexpr uint32_t kCtrlBytes = 256;          // mbarriers, TMEM address, abort flag
 constexpr long long kWaitLimit = 4000000000LL;  // clock cycles (about 2 s)
 constexpr uint32_t kSuspendNs = 1000000;        // longest suspension of one phase test
+
+// Compile-time shape of one kernel instance: KC 64-wide K chunks per stage
+// (1: order <= 64, 2: order <= 96), NG groups of five tracers per kind.
+template <int KC, int NG> struct TcCfg {
+    static constexpr int LV = KC == 1 ? 5 : 4;              // TMEM accumulator levels
+    static constexpr int kStages = KC == 1 ? (NG == 1 ? 8 : 6) : (NG == 1 ? 4 : 3);
+    static constexpr uint32_t kStageBytes = KC * kS * kBSliceBytes;
+    static constexpr uint32_t kACol = kNBUF * LV * kQT;     // TMEM column of the coefficient slices
+    static constexpr int kYbufFloats = 2 * 4 * NG * kNB * 64; // [parity][quadrant][tracer][hi, lo][lane]
+    static constexpr size_t kVsmBytes = NG == 2 ? (size_t)kNB * (kHC / 2) * 128 * kEP * 8 : 0;
+    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kCtrlBytes + kYbufFloats * 4 + kVsmBytes;
+};
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -166,17 +184,31 @@ __device__ __forceinline__ bool elect_one()
     return p != 0;
 }
 
-// Thirty-two consecutive 32-bit columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+// Eight consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
 {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
-        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
-        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]),
-        "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
-        : "memory");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld4(uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
+}
+
+// Register fence for values a tcgen05.wait::ld has already covered: ties
+// them to a point after that wait.
+__device__ __forceinline__ void reg_fence4(uint32_t (&r)[4])
+{
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -186,14 +218,6 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
-}
-
-// Four consecutive 32-bit columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
 }
 
 // Knuth's two-sum: s + e == a + b exactly, s = fl(a + b).
@@ -272,21 +296,21 @@ __device__ __forceinline__ void two_sum2(f32x2 a, f32x2 b, f32x2 &s, f32x2 &e)
     s = ss;
 }
 
-// Wait for this thread's TMEM loads of four columns per level; the registers
-// they fill are operands, so no use of them can move above the wait.
-__device__ __forceinline__ void tmem_wait_ld4(uint32_t (&r)[BLAST_TC_SLICES][4])
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// One-dimensional bulk copy global -> shared (both 16-byte aligned, size a
+// multiple of 16) completing on an mbarrier of this CTA.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[1][0]), "+r"(r[1][1]),
-                   "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]),
-                   "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]), "+r"(r[4][0]), "+r"(r[4][1]),
-                   "+r"(r[4][2]), "+r"(r[4][3])
-                 :
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
 
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// Order this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---------------------------------------------------------------- slicing
 // x (|x| < 1) -> S slices: integers in [-256, 256] times 2^(-8p) f for slice
@@ -305,10 +329,13 @@ __device__ __forceinline__ void slice8(double xn, uint16_t (&out)[kS], float f =
     }
 }
 
-// Coefficient slices, one warp per cosmology: A_p[b][n] and 2^ea(b); also the
-// chi weights U transposed to cosmology-fastest order for the reduction.
-__global__ void k_coef_slices(const ReqDev *__restrict__ reqs, int n, int N, int Kp, int Bpad, uint16_t *A,
-                              float *sa, int X, int ntr_max, float *UT, float *UTl)
+// Coefficient slices, one warp per cosmology: A_p[b][k] (k < Kst, zero past
+// the order) and 2^ea(b); also the chi weights U of both tracer kinds as
+// (hi, lo) FP32 pairs, laid out for the reduction's bulk copies:
+//   U[bt][a][kind][hl][i][lane],  b = 32 bt + lane,  i < MT (zero past the
+//   request's tracer count), kind 0 clustering, 1 lensing.
+__global__ void k_coef_slices(const ReqDev *__restrict__ reqs, int n, int N, int Kst, int Bpad, uint16_t *A,
+                              float *sa, int X, int MT, float *U)
 {
     const int b = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
     if (b >= Bpad) return;
@@ -318,30 +345,36 @@ __global__ void k_coef_slices(const ReqDev *__restrict__ reqs, int n, int N, int
     for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
-    for (int k = lane; k < Kp; k += 32) {
+    for (int k = lane; k < Kst; k += 32) {
         uint16_t s[kS];
         slice8((a && k < N) ? ldexp(a[k], -e) : 0.0, s);
 #pragma unroll
-        for (int p = 0; p < kS; p++) A[((size_t)p * Bpad + b) * Kp + k] = s[p];
+        for (int p = 0; p < kS; p++) A[((size_t)p * Bpad + b) * Kst + k] = s[p];
     }
     if (lane == 0) sa[b] = ldexpf(1.0f, e);
-    const int ntr = (b < n) ? reqs[b].n_clust + reqs[b].n_lens : 0;
-    const double *U = (b < n) ? reqs[b].U64 : nullptr;
-    for (int i = lane; i < ntr_max * X; i += 32) {
-        const double u = (i < ntr * X) ? U[i] : 0.0;
+    const int ng = (b < n) ? reqs[b].n_clust : 0, ns = (b < n) ? reqs[b].n_lens : 0;
+    const double *Uq = (b < n) ? reqs[b].U64 : nullptr;
+    const int bt = b >> 5, bl = b & 31;
+    for (int idx = lane; idx < 2 * MT * X; idx += 32) {
+        const int kind = idx / (MT * X), i = (idx / X) % MT, a_ = idx % X;
+        const int cnt = kind ? ns : ng, row = kind ? ng + i : i;
+        const double u = (i < cnt) ? Uq[(size_t)row * X + a_] : 0.0;
         const float uh = (float)u;
-        UT[(size_t)i * Bpad + b] = uh;
-        UTl[(size_t)i * Bpad + b] = (float)(u - (double)uh);
+        float *dst = U + ((((size_t)bt * X + a_) * 2 + kind) * 2) * MT * 32 + (size_t)i * 32 + bl;
+        dst[0] = uh;
+        dst[(size_t)MT * 32] = (float)(u - (double)uh);
     }
 }
 
 // Basis slices, one warp per tile of kQT columns (t, l, q0..q0+31), a lane per
-// column: T_p[col][n] 2^(-8p) 2^(eT(col) - eG) with eG the largest column
-// exponent of the tile, and one scale 2^(eG - 16) per tile.  A column keeps
-// its own 40-bit fixed-point precision; the power of two moves the exponent
-// only.  Columns more than 2^90 below the tile's largest (or in tiles whose
-// scale underflows FP32) are zero: they could not change the tile's sum.
-__global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q, int Kp, uint16_t *Tsl, float *scT)
+// column: T_p[col][k] 2^(-8p) 2^(eT(col) - eG) (k < Kst, zero past the order)
+// with eG the largest column exponent of the tile, and one scale 2^(eG - 16)
+// per tile.  A column keeps its own 40-bit fixed-point precision; the power of
+// two moves the exponent only.  Columns more than 2^90 below the tile's
+// largest (or in tiles whose scale underflows FP32) are zero: they could not
+// change the tile's sum.
+__global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q, int Kst, uint16_t *Tsl,
+                               float *scT)
 {
     const size_t ncol = (size_t)3 * L * Q;
     const size_t ntile = ncol / kQT;
@@ -360,11 +393,11 @@ __global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q
         const float scf = (eG != INT_MIN) ? (float)ldexp(1.0, eG - 16) : 0.0f;
         const bool keep = mx > 0.0 && scf != 0.0f && e - eG >= -90;
         const float shift = keep ? ldexpf(1.0f, e - eG) : 0.0f;
-        for (int k = 0; k < Kp; k++) {
+        for (int k = 0; k < Kst; k++) {
             uint16_t s[kS];
             slice8((k < N && keep) ? ldexp(src[(size_t)k * Q], -e) : 0.0, s, shift);
 #pragma unroll
-            for (int p = 0; p < kS; p++) Tsl[((size_t)p * ncol + col) * Kp + k] = s[p];
+            for (int p = 0; p < kS; p++) Tsl[((size_t)p * ncol + col) * Kst + k] = s[p];
         }
         if (lane == 0) scT[tile] = scf;
     }
@@ -373,29 +406,34 @@ __global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q
 // ---------------------------------------------------------------- main kernel
 struct TcArgs {
     const ReqDev *reqs;
-    int n, Bpad, nbt, nqt, n_esel, L, Q, Rn, RT, MT;
+    int n, Bpad, nbt, nqt, n_esel, L, Q, Rn, RT, MT, X, Kst, Kmma;
     const int *esel;
     const float *scT;    // [3][L][Q / kQT] one scale per tile
     const float *sa;     // [Bpad]
-    const uint16_t *A;   // [S][Bpad][64] coefficient slices
-    float *Y;            // [3][n_esel][X][n][RT][MT] pairs (hi, lo)
+    const uint16_t *A;   // [S][Bpad][Kst] coefficient slices
+    float *Y;            // [3][n_esel][X][Bpad/32][RT][MT][hi, lo][32] R-tile partial pairs
     int *err;            // host-mapped error word
 };
 
+template <int KC, int NG>
 __global__ void __launch_bounds__(kThreads, 1)
 k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
 {
+    using C = TcCfg<KC, NG>;
+    constexpr int LV = C::LV;
+    constexpr int kStages = C::kStages;
+    constexpr int NGB = NG * kNB;  // tracers per kind this instance serves
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sB = smem;                                  // kStages x kS x 4 KB
-    uint64_t *bars = (uint64_t *)(sB + kStages * kBStageBytes);  // kCtrlBytes of control words
+    unsigned char *sB = smem;                                         // kStages x KC x kS x 4 KB
+    uint64_t *bars = (uint64_t *)(sB + (size_t)kStages * C::kStageBytes);  // kCtrlBytes of control words
     uint64_t *full = bars, *empty = bars + kStages, *aready = bars + 2 * kStages;
-    uint64_t *tfull = aready + 1, *tempty = tfull + 2;
-    uint32_t *tmem_slot = (uint32_t *)(tempty + 2);
+    uint64_t *tfull = aready + 1, *tempty = tfull + kNBUF, *mdone = tempty + kNBUF;
+    uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    float *ybuf = (float *)((unsigned char *)bars + kCtrlBytes);   // [2][kEP-1][2 kNB][kM] partial pairs
-    f32x2 *vsm = (f32x2 *)(ybuf + 2 * (kEP - 1) * 2 * kNB * kM);   // [kNB][kHC/2][128 kEP] weights
+    float *ybuf = (float *)((unsigned char *)bars + kCtrlBytes);       // [2][4][NGB][2][32] column-half hand-over
+    f32x2 *vsm = (f32x2 *)(ybuf + C::kYbufFloats);                    // [kNB][kHC/2][256] weights of tracers 5..9
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int btile = blockIdx.x % args.nbt;
@@ -404,9 +442,8 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; i++) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         mbar_init(aready, 128);
-        for (int i = 0; i < 2; i++) {
-            mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128 * kEP);
-        }
+        for (int i = 0; i < kNBUF; i++) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128 * kEP); }
+        mbar_init(mdone, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -438,14 +475,17 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                 if (elect_one()) {
                     const int t = it / args.n_esel, e = args.esel[it % args.n_esel];
                     const int row = (t * args.L + e) * args.Q + q0;
-                    mbar_expect_tx(&full[st], kBStageBytes);
-                    tma_load_3d(sB + st * kBStageBytes, &mapB, &full[st], 0, row, 0);
+                    mbar_expect_tx(&full[st], C::kStageBytes);
+#pragma unroll
+                    for (int c = 0; c < KC; c++)
+                        tma_load_3d(sB + (size_t)st * C::kStageBytes + c * kS * kBSliceBytes, &mapB, &full[st],
+                                    c * kKC, row, 0);
                 }
                 __syncwarp();
             }
         }
         // drain: every issued load has landed before the CTA may exit
-        for (uint32_t h = (g > kStages ? g - kStages : 0); h < g; h++)
+        for (uint32_t h = (g > (uint32_t)kStages ? g - kStages : 0); h < g; h++)
             mbar_wait(&full[h % kStages], (h / kStages) & 1, 64);
         __syncwarp();
     } else if (warp == 1) {
@@ -456,13 +496,15 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         tc_fence_after();
         const uint32_t b0 = __shfl_sync(0xffffffffu, smem_u32(sB), 0);  // warp-uniform operands
         const uint32_t tm = __shfl_sync(0xffffffffu, tmem, 0);
+        const int nk = args.Kmma / 16;        // K steps of 16
+        const uint32_t acol = args.Kmma / 2;  // TMEM columns per coefficient slice
         uint32_t g = 0;
         for (int u = blockIdx.x; ok && u < args.nbt * args.nqt; u += gridDim.x) {
             for (int it = 0; it < n_iter_unit; it++, g++) {
                 const int st = g % kStages;
                 const uint32_t ph = (g / kStages) & 1;
-                const int buf = g & 1;
-                const uint32_t tph = (g >> 1) & 1;
+                const int buf = g % kNBUF;
+                const uint32_t tph = (g / kNBUF) & 1;
                 const bool bad = *abort_flag || !mbar_wait(&full[st], ph, 64) || !mbar_wait(&tempty[buf], tph ^ 1, 64);
                 if (__any_sync(0xffffffffu, bad)) {
                     if (lane == 0) { atomicExch(args.err, 3); *abort_flag = 1; }
@@ -470,20 +512,26 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                     break;
                 }
                 tc_fence_after();
-                // operands of the 60 MMAs: accumulator levels of this buffer, coefficient
-                // slices in TMEM, basis slice descriptors offset from this stage's first
-                const uint32_t dbase = tm + buf * (kS * kQT);
-                const uint64_t bbase = sdesc(b0 + st * kBStageBytes);
+                // operands: accumulator levels of this buffer, coefficient slices in
+                // TMEM, basis slice descriptors offset from this stage's first
+                const uint32_t dbase = tm + buf * (LV * kQT);
+                const uint64_t bbase = sdesc(b0 + st * C::kStageBytes);
                 if (elect_one()) {
 #pragma unroll
-                    for (int lev = 0; lev < kS; lev++) {
+                    for (int lev = 0; lev < LV; lev++) {
+                        uint32_t acc = 0;
 #pragma unroll
-                        for (int p = 0; p <= lev; p++) {
-                            const int q = lev - p;
+                        for (int p = 0; p < kS; p++) {
 #pragma unroll
-                            for (int kk = 0; kk < kKC / 16; kk++)
-                                umma_ts(dbase + lev * kQT, tm + kACol + p * (kKC / 2) + kk * 8,
-                                        bbase + (uint64_t)((q * kBSliceBytes + kk * 32) >> 4), (p > 0 || kk > 0) ? 1u : 0u);
+                            for (int q = 0; q < kS - p; q++) {
+                                if ((p + q < LV - 1 ? p + q : LV - 1) != lev) continue;
+                                for (int kk = 0; kk < nk; kk++) {
+                                    const uint32_t boff = (kk >> 2) * (kS * kBSliceBytes) + q * kBSliceBytes + (kk & 3) * 32;
+                                    umma_ts(dbase + lev * kQT, tm + C::kACol + p * acol + kk * 8,
+                                            bbase + (uint64_t)(boff >> 4), acc);
+                                    acc = 1;
+                                }
+                            }
                         }
                     }
                 }
@@ -495,6 +543,11 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                 __syncwarp();
             }
         }
+        // every MMA this warp issued has completed before TMEM is released
+        if (elect_one()) umma_commit(mdone);
+        __syncwarp();
+        mbar_wait(mdone, 0, 64);
+        __syncwarp();
     } else {
         // ------------------------------------------------ epilogue: kEP warps per TMEM lane quadrant;
         // a thread owns one cosmology (TMEM lane) and kHC of the tile's 32 columns.
@@ -509,38 +562,38 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         const float sa = args.sa[b];
         const uint32_t lane_addr = ((uint32_t)(quad * 32)) << 16;
         const int cb = part * kHC;
+        const int tid_e = threadIdx.x - 64;  // 0 .. 128 kEP - 1
         if (part == 0) {
-            // coefficient slices of cosmology b -> TMEM lane b, columns kACol + 32 p ..
+            // coefficient slices of cosmology b -> TMEM lane b, columns kACol + (Kmma/2) p ..
+            const int acol = args.Kmma / 2;
 #pragma unroll 1
             for (int p = 0; p < kS; p++) {
-                uint32_t r[32];
-                const uint4 *src = reinterpret_cast<const uint4 *>(args.A + ((size_t)p * args.Bpad + b) * kKC);
-#pragma unroll
-                for (int i = 0; i < 8; i++) {
-                    const uint4 v = __ldg(src + i);
-                    r[4 * i] = v.x; r[4 * i + 1] = v.y; r[4 * i + 2] = v.z; r[4 * i + 3] = v.w;
+                const uint4 *src = reinterpret_cast<const uint4 *>(args.A + ((size_t)p * args.Bpad + b) * args.Kst);
+#pragma unroll 1
+                for (int c8 = 0; c8 < acol / 8; c8++) {
+                    const uint4 v0 = __ldg(src + 2 * c8), v1 = __ldg(src + 2 * c8 + 1);
+                    const uint32_t r[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                    tmem_st8(tmem + lane_addr + C::kACol + p * acol + c8 * 8, r);
                 }
-                tmem_st32(tmem + lane_addr + kACol + p * (kKC / 2), r);
             }
             tmem_wait_st();
             tc_fence_before();
             mbar_arrive(aready);
         }
-        // Every thread of the quadrant's four warps passes the same number of
+        // Every thread of the quadrant's two warps passes the same number of
         // named barriers; after a wait runs out the warps skip the work but keep
         // the count, so no barrier is left waiting.
         const int bar_id = 1 + quad;
         uint32_t g = 0;
         bool dead = false;
+        f32x2 vr[kNB][kHC / 2];  // quadrature weights (times 2^ea) of tracers 0..4 of the B-side kind
         for (int u = blockIdx.x; u < args.nbt * args.nqt; u += gridDim.x) {
             const int q0 = (u / args.nbt) * kQT;
             const int a = q0 / args.Rn, rt = (q0 % args.Rn) / kQT;
-            // quadrature weights of this cosmology times its scale 2^ea, kept in this
-            // thread's own slots of shared memory (read back only by this thread)
-            f32x2 *vme = vsm + (threadIdx.x - 64);
             for (int t = 0; t < 3; t++) {
                 const int offB = (t == 0) ? 0 : ng, nB = (t == 0) ? ng : ns;
                 if (t < 2) {
+                    // weights of the B-side kind: clustering for gg, lensing for gs and ss
 #pragma unroll
                     for (int j = 0; j < kNB; j++) {
                         const float4 *src =
@@ -550,14 +603,28 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
 #pragma unroll
                         for (int c = 0; c < kHC / 4; c++) {
                             const float4 v = src ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-                            vme[(j * (kHC / 2) + 2 * c) * (128 * kEP)] = pk2(v.x * sa, v.y * sa);
-                            vme[(j * (kHC / 2) + 2 * c + 1) * (128 * kEP)] = pk2(v.z * sa, v.w * sa);
+                            vr[j][2 * c] = pk2(v.x * sa, v.y * sa);
+                            vr[j][2 * c + 1] = pk2(v.z * sa, v.w * sa);
+                        }
+                    }
+                    if (NG == 2) {  // tracers 5..9 in this thread's own shared-memory slots
+                        for (int j = 0; j < kNB; j++) {
+                            const float4 *src = (valid && kNB + j < nB)
+                                                    ? reinterpret_cast<const float4 *>(
+                                                          rq->V32 + (size_t)(offB + kNB + j) * args.Q + q0 + cb)
+                                                    : nullptr;
+#pragma unroll
+                            for (int c = 0; c < kHC / 4; c++) {
+                                const float4 v = src ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+                                vsm[(j * (kHC / 2) + 2 * c) * (128 * kEP) + tid_e] = pk2(v.x * sa, v.y * sa);
+                                vsm[(j * (kHC / 2) + 2 * c + 1) * (128 * kEP) + tid_e] = pk2(v.z * sa, v.w * sa);
+                            }
                         }
                     }
                 }
                 for (int es = 0; es < args.n_esel; es++, g++) {
-                    const int buf = g & 1;
-                    const uint32_t tph = (g >> 1) & 1;
+                    const int buf = g % kNBUF;
+                    const uint32_t tph = (g / kNBUF) & 1;
                     if (!dead) {
                         bool lost = *abort_flag != 0;
                         if (!lost && !mbar_wait(&tfull[buf], tph)) {
@@ -567,72 +634,77 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                         }
                         dead = __any_sync(0xffffffffu, lost);
                     }
-                    float Sh[kNB], Sl[kNB];
+                    float Sh[NGB], Sl[NGB];
 #pragma unroll
-                    for (int j = 0; j < kNB; j++) { Sh[j] = 0.f; Sl[j] = 0.f; }
+                    for (int j = 0; j < NGB; j++) { Sh[j] = 0.f; Sl[j] = 0.f; }
                     if (!dead) {
                         tc_fence_after();
-                        const uint32_t tcol = tmem + lane_addr + buf * (kS * kQT) + cb;
+                        const uint32_t tcol = tmem + lane_addr + buf * (LV * kQT) + cb;
                         // R-sum of this thread's columns, two columns per packed lane pair, as
                         // negated unevaluated sums An + Bn: each product V w is split exactly
-                        // (FMA) and each addition's rounding error is kept (two-sum), so the
+                        // (FMA), the two products of a lane pair are added plainly, and each
+                        // addition of those sums keeps its rounding error (two-sum), so the
                         // sum survives the cancellation of oscillating w
-                        f32x2 An[kNB], Bn[kNB];
-                        // four columns (two packed pairs) per step: pair A = columns c0, c0+1
-                        // in lanes x, y; pair B = c0+2, c0+3.  Each lane's two exact products
-                        // (columns two R nodes apart) are added plainly, and that sum enters
-                        // the compensated sum
+                        f32x2 An[NGB], Bn[NGB];
 #pragma unroll
-                        for (int c0 = 0; c0 < kHC; c0 += 4) {
-                            uint32_t D[kS][4];
+                        for (int s = 0; s < kHC / kCS; s++) {
+                            uint32_t D[LV][kCS];
 #pragma unroll
-                            for (int lev = 0; lev < kS; lev++) tmem_ld4(tcol + lev * kQT + c0, D[lev]);
-                            tmem_wait_ld4(D);
-                            if (c0 + 4 == kHC) {  // every level of this buffer is in registers: release it
+                            for (int lev = 0; lev < LV; lev++) tmem_ld4(tcol + lev * kQT + s * kCS, D[lev]);
+                            tmem_wait_ld4(D[0]);
+#pragma unroll
+                            for (int lev = 1; lev < LV; lev++) reg_fence4(D[lev]);
+                            if (s + 1 == kHC / kCS) {  // every level of this buffer is in registers: release it
                                 tc_fence_before();
                                 mbar_arrive(&tempty[buf]);
                             }
-                            // Level k holds D_k 2^(-8k) 2^(eT - eG), an integer multiple of
-                            // 2^(-8k) 2^(eT - eG) below 2^(23-8k) 2^(eT - eG) in magnitude, so
-                            // every fast two-sum of the cascade is exact:
-                            // W 2^(eT - eG - 32) = m + (e1 + e2 + e3 + e4), one rounding in the
-                            // low part only
-                            f32x2 m[2], lo[2];
+                            // levels 0..2 are exact multiples of their quanta, so both fast
+                            // two-sums are exact; the small parts add plainly (one rounding)
+                            f32x2 m[kCS / 2], lo[kCS / 2];
 #pragma unroll
-                            for (int h = 0; h < 2; h++) {
-                                f32x2 d[kS];
+                            for (int h = 0; h < kCS / 2; h++) {
+                                f32x2 d[LV];
 #pragma unroll
-                                for (int lev = 0; lev < kS; lev++)
+                                for (int lev = 0; lev < LV; lev++)
                                     d[lev] = pk2(__uint_as_float(D[lev][2 * h]), __uint_as_float(D[lev][2 * h + 1]));
-                                f32x2 e1, e2, e3, e4;
+                                f32x2 e1, e2;
                                 fast_two_sum2(d[0], d[1], m[h], e1);
                                 fast_two_sum2(m[h], d[2], m[h], e2);
-                                fast_two_sum2(m[h], d[3], m[h], e3);
-                                fast_two_sum2(m[h], d[4], m[h], e4);
-                                lo[h] = add2(add2(e1, e2), add2(e3, e4));
+                                const f32x2 small = (LV == 5) ? add2(d[3], d[LV - 1]) : d[3];
+                                lo[h] = add2(add2(e1, e2), small);
                             }
-                            const f32x2 mn0 = neg2(m[0]), mn1 = neg2(m[1]);
 #pragma unroll
-                            for (int j = 0; j < kNB; j++) {
-                                const f32x2 v0 = vme[(j * (kHC / 2) + c0 / 2) * (128 * kEP)];
-                                const f32x2 v1 = vme[(j * (kHC / 2) + c0 / 2 + 1) * (128 * kEP)];
-                                const f32x2 p0 = mul2(v0, mn0), p1 = mul2(v1, mn1);  // -fl(v m)
-                                const f32x2 e0 = fma2(v0, lo[0], fma2(v0, m[0], p0));  // v lo + (v m - fl(v m))
-                                const f32x2 e1 = fma2(v1, lo[1], fma2(v1, m[1], p1));
-                                const f32x2 ps = add2(p0, p1), pe = add2(e0, e1);
-                                if (c0 == 0) {  // the sums start here
-                                    An[j] = ps;
-                                    Bn[j] = neg2(pe);
-                                } else {
-                                    f32x2 se;
-                                    two_sum2(An[j], ps, An[j], se);
-                                    Bn[j] = add2(Bn[j], sub2(se, pe));
+                            for (int ch = 0; ch < kCS / 4; ch++) {
+                                const int h0 = 2 * ch, h1 = 2 * ch + 1;
+                                const f32x2 mn0 = neg2(m[h0]), mn1 = neg2(m[h1]);
+                                const bool first = (s == 0 && ch == 0);
+#pragma unroll
+                                for (int j = 0; j < NGB; j++) {
+                                    const int pc = s * (kCS / 2) + h0;  // packed column pair index
+                                    f32x2 v0, v1;
+                                    if (j < kNB) { v0 = vr[j][pc]; v1 = vr[j][pc + 1]; }
+                                    else {
+                                        v0 = vsm[((j - kNB) * (kHC / 2) + pc) * (128 * kEP) + tid_e];
+                                        v1 = vsm[((j - kNB) * (kHC / 2) + pc + 1) * (128 * kEP) + tid_e];
+                                    }
+                                    const f32x2 p0 = mul2(v0, mn0), p1 = mul2(v1, mn1);   // -fl(v m)
+                                    const f32x2 e0 = fma2(v0, lo[h0], fma2(v0, m[h0], p0));  // v lo + (v m - fl(v m))
+                                    const f32x2 e1 = fma2(v1, lo[h1], fma2(v1, m[h1], p1));
+                                    const f32x2 ps = add2(p0, p1), pe = add2(e0, e1);
+                                    if (first) {  // the sums start here
+                                        An[j] = ps;
+                                        Bn[j] = neg2(pe);
+                                    } else {
+                                        f32x2 se;
+                                        two_sum2(An[j], ps, An[j], se);
+                                        Bn[j] = add2(Bn[j], sub2(se, pe));
+                                    }
                                 }
                             }
                         }
                         // both lanes into one pair per tracer: S = -(An.x + An.y) - (Bn.x + Bn.y)
 #pragma unroll
-                        for (int j = 0; j < kNB; j++) {
+                        for (int j = 0; j < NGB; j++) {
                             const float2 A2 = unpk2(An[j]), B2 = unpk2(Bn[j]);
                             float h, el;
                             two_sum(A2.x, A2.y, h, el);
@@ -640,41 +712,32 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                             Sl[j] = -__fadd_rn(el, __fadd_rn(B2.x, B2.y));
                         }
                     }
-                    // add the column parts: parts 1.. hand their pairs to part 0 through
-                    // shared memory ([part - 1][2 kNB][kM], double buffered by iteration)
-                    float *yq = ybuf + (size_t)(g & 1) * (kEP - 1) * 2 * kNB * kM;
-                    if (part > 0) {
-                        float *slot = yq + (size_t)(part - 1) * 2 * kNB * kM + bl_;
+                    // the column halves meet: part 1 hands its pairs to part 0 through
+                    // shared memory, double buffered by iteration
+                    float *yq = ybuf + ((size_t)(g & 1) * 4 + quad) * (NGB * 64);
+                    if (part == 1) {
 #pragma unroll
-                        for (int j = 0; j < kNB; j++) { slot[j * kM] = Sh[j]; slot[(kNB + j) * kM] = Sl[j]; }
+                        for (int j = 0; j < NGB; j++) { yq[j * 64 + lane] = Sh[j]; yq[j * 64 + 32 + lane] = Sl[j]; }
                     }
                     named_bar_sync(bar_id, 32 * kEP);
                     if (part == 0 && !dead) {
 #pragma unroll
-                        for (int q = 0; q < kEP - 1; q++) {
-                            const float *slot = yq + (size_t)q * 2 * kNB * kM + bl_;
-#pragma unroll
-                            for (int j = 0; j < kNB; j++) {
-                                float se;
-                                two_sum(Sh[j], slot[j * kM], Sh[j], se);
-                                Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, slot[(kNB + j) * kM]));
-                            }
+                        for (int j = 0; j < NGB; j++) {
+                            float se;
+                            two_sum(Sh[j], yq[j * 64 + lane], Sh[j], se);
+                            Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, yq[j * 64 + 32 + lane]));
                         }
                         if (valid) {
-                            // the tile's scale 2^(eG - 16) (exact), then the pair (hi, lo)
-                            // of tracer j at j and MT + j
+                            // the tile's scale 2^(eG - 16) (exact); the pair (hi, lo) of tracer j
+                            // at Y[t][es][a][b / 32][rt][j][hi, lo][b % 32]: a warp stores 128 bytes
                             const float tsc =
                                 args.scT[((size_t)t * args.L + args.esel[es]) * (args.Q / kQT) + q0 / kQT];
+                            float *y = args.Y +
+                                       (((((size_t)t * args.n_esel + es) * args.X + a) * (args.Bpad / 32) + (b >> 5)) *
+                                            args.RT + rt) * (size_t)args.MT * 64 + lane;
 #pragma unroll
-                            for (int j = 0; j < kNB; j++) { Sh[j] *= tsc; Sl[j] *= tsc; }
-                            // Y[t][es][a][b][rt][j] pairs (hi, lo): one cosmology's R tiles of a
-                            // chi node are contiguous for the reduction's vector loads
-                            float2 *y = reinterpret_cast<float2 *>(args.Y) +
-                                        ((((size_t)t * args.n_esel + es) * (args.Q / args.Rn) + a) * args.n + b) *
-                                            (size_t)(args.RT * args.MT) + (size_t)rt * args.MT;
-#pragma unroll
-                            for (int j = 0; j < kNB; j++)
-                                if (j < args.MT) y[j] = make_float2(Sh[j], Sl[j]);
+                            for (int j = 0; j < NGB; j++)
+                                if (j < args.MT) { y[j * 64] = Sh[j] * tsc; y[j * 64 + 32] = Sl[j] * tsc; }
                         }
                     }
                 }
@@ -689,116 +752,96 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     }
 }
 
-// A thread's staging slot of k_reduce_tc in float2 units: RT MT pairs and the
-// kNB + kNB chi weights, rounded up to 16 bytes so every slot is 16-byte aligned.
-__host__ __device__ __forceinline__ int reduce_slot_f2(int RT, int MT) { return (RT * MT + kNB + 1) & ~1; }
-
-// Asynchronous global -> shared copies (cp.async): 16, 8 or 4 bytes each,
-// visible to the issuing thread after the matching wait_group.
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Sum over R tiles and chi nodes for the tensor-core path, one thread per
-// (cosmology, type, ell, chi chunk) accumulating every tracer pair (i, j):
+// Sum over R tiles and chi nodes for the tensor-core path.  A block handles
+// (32 cosmologies, selected ell, type, A-side tracer group of five) and W
+// warps split the chi nodes; a thread owns one cosmology and accumulates every
+// tracer pair (i, j) of its group:
 //   s_j(a) = sum_rt Y(t, l, a, rt, j)          (pairs (hi, lo), two-sum)
 //   C_ij(l) = N_AB(l) sum_a U_i(a) s_j(a)      (exact products, two-sum)
-// A block is 32 cosmologies x W chi chunks (one warp each).  Each thread
-// streams its own R-tile pairs and chi weights of the next STG - 1 chi nodes
-// into its own shared-memory slots with cp.async while it sums the current
-// one, so enough bytes are in flight to keep HBM busy; the chunks are then
-// added in a tree through the same shared memory.
-template <int W, int STG>
-__global__ void __launch_bounds__(32 * W, 2)
-k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const float *__restrict__ UT,
-            const float *__restrict__ UTl, int n, int Bpad, int X, int L, const int *__restrict__ esel, int n_esel,
-            int RT, int MT, const double *__restrict__ pref)
+// Each warp streams its chi nodes through a ring of NS shared-memory stages:
+// one bulk copy brings the 32 cosmologies' R-tile pairs of a chi node
+// (contiguous in Y), another their chi weights; the chunks meet in a tree
+// through the same shared memory at the end.
+template <int MTT>
+__global__ void __launch_bounds__(256)
+k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const float *__restrict__ U, int n,
+            int X, int L, const int *__restrict__ esel, int n_esel, int RT, int MT, int nbt32, int NS,
+            const double *__restrict__ pref, int *err)
 {
-    extern __shared__ __align__(16) unsigned char red_smem[];
-    const int lane = threadIdx.x & 31, chunk = threadIdx.x >> 5;
-    const int b = blockIdx.x * 32 + lane;
-    const int es = blockIdx.y, t = blockIdx.z;
+    constexpr int NIG = MTT / kNB;  // A-side tracer groups
+    extern __shared__ __align__(128) unsigned char red_smem[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int bt = blockIdx.x, es = blockIdx.y;
+    const int t = blockIdx.z / NIG, ig = blockIdx.z % NIG;
+    const int b = bt * 32 + lane;
     const ReqDev *rq = (b < n) ? &reqs[b] : nullptr;
     const int ng = rq ? rq->n_clust : 0, ns = rq ? rq->n_lens : 0;
-    const int nA = (t == 2) ? ns : ng, nB = (t == 0) ? ng : ns, offA = (t == 2) ? ng : 0;
+    const int nA = (t == 2) ? ns : ng, nB = (t == 0) ? ng : ns, kindA = (t == 2) ? 1 : 0;
     const int e = esel[es];
     const int col = rq ? rq->e_out[e] : -1;
-    const bool active = rq && nA > 0 && nB > 0 && col >= 0;
-    // per thread and stage: RT MT pairs (hi, lo), then U hi[kNB], U lo[kNB]
-    const int RTMT = RT * MT;
-    const int slot_f2 = reduce_slot_f2(RT, MT);
-    float2 *my = reinterpret_cast<float2 *>(red_smem) + ((size_t)chunk * STG * 32 + lane) * slot_f2;
-    auto stage_ptr = [&](int st) { return my + (size_t)st * 32 * slot_f2; };
+    const int yfl = RT * MT * 64, ufl = 2 * MT * 32, stf = yfl + ufl;  // floats per stage
+    float *ring = reinterpret_cast<float *>(red_smem) + (size_t)w * NS * stf;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<float *>(red_smem) + (size_t)W * NS * stf) + w * NS;
+    if (lane == 0) {
+        for (int s = 0; s < NS; s++) mbar_init(&bars[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
     const int per = (X + W - 1) / W;
-    const int a0 = chunk * per, a1 = min(X, a0 + per);
-    const int cnt = active ? max(0, a1 - a0) : 0;
-    const float2 *Yb = reinterpret_cast<const float2 *>(Y) + ((size_t)t * n_esel + es) * (size_t)X * n * RTMT +
-                       (size_t)b * RTMT;
-    const bool even = (RTMT & 1) == 0;  // 16-byte copies when each thread's pairs are 16-byte aligned
-    auto issue = [&](int k) {           // copies of chi node a0 + k into stage k % STG
-        if (k < cnt) {
-            float2 *d = stage_ptr(k % STG);
-            const float2 *y = Yb + (size_t)(a0 + k) * n * RTMT;
-            if (even)
-                for (int i = 0; i < RTMT; i += 2) cp_async16(d + i, y + i);
-            else
-                for (int i = 0; i < RTMT; i++) cp_async8(d + i, y + i);
-            float *u = reinterpret_cast<float *>(d + RTMT);
-            for (int i = 0; i < nA; i++) {
-                const size_t ui = ((size_t)(offA + i) * X + a0 + k) * Bpad + b;
-                cp_async4(u + i, UT + ui);
-                cp_async4(u + kNB + i, UTl + ui);
-            }
+    const int a0 = w * per, cnt = max(0, min(X, a0 + per) - a0);
+    const float *Yb = Y + ((size_t)t * n_esel + es) * (size_t)X * nbt32 * yfl + (size_t)bt * yfl;
+    const float *Ub = U + (size_t)bt * X * 2 * ufl + (size_t)kindA * ufl;
+    auto issue = [&](int k) {  // chi node a0 + k into stage k % NS
+        if (k < cnt && lane == 0) {
+            float *d = ring + (size_t)(k % NS) * stf;
+            const int a = a0 + k;
+            fence_proxy_async();
+            mbar_expect_tx(&bars[k % NS], (uint32_t)stf * 4);
+            bulk_g2s(d, Yb + (size_t)a * nbt32 * yfl, (uint32_t)yfl * 4, &bars[k % NS]);
+            bulk_g2s(d + yfl, Ub + (size_t)a * 2 * ufl, (uint32_t)ufl * 4, &bars[k % NS]);
         }
-        cp_async_commit();  // every thread commits every step: group counts stay uniform
     };
-    float Zh[kNB][kNB], Zl[kNB][kNB];
+    for (int k = 0; k < NS; k++) issue(k);
+    float Zh[kNB][MTT], Zl[kNB][MTT];
 #pragma unroll
     for (int i = 0; i < kNB; i++)
 #pragma unroll
-        for (int j = 0; j < kNB; j++) { Zh[i][j] = 0.f; Zl[i][j] = 0.f; }
+        for (int j = 0; j < MTT; j++) { Zh[i][j] = 0.f; Zl[i][j] = 0.f; }
+    int done = 0;  // chi nodes whose stage was consumed
+    bool aborted = false;
+    for (int k = 0; k < cnt; k++, done++) {
+        const bool bad = !mbar_wait(&bars[k % NS], (k / NS) & 1);
+        if (__any_sync(0xffffffffu, bad)) {
+            if (lane == 0) atomicExch(err, 5);
+            aborted = true;
+            break;
+        }
+        const float *v = ring + (size_t)(k % NS) * stf;
+        float sh[MTT], sl[MTT];
 #pragma unroll
-    for (int k = 0; k < STG - 1; k++) issue(k);
-    for (int k = 0; k < per; k++) {
-        issue(k + STG - 1);
-        cp_async_wait<STG - 1>();  // node a0 + k has landed
-        if (k >= cnt) continue;
-        const float2 *v = stage_ptr(k % STG);
-        float sh[kNB], sl[kNB];
-#pragma unroll
-        for (int j = 0; j < kNB; j++) { sh[j] = 0.f; sl[j] = 0.f; }
-        for (int rt = 0; rt < RT; rt++) {
-#pragma unroll
-            for (int j = 0; j < kNB; j++) {
-                if (j < nB) {
-                    const float2 y = v[rt * MT + j];
+        for (int j = 0; j < MTT; j++) {
+            sh[j] = 0.f;
+            sl[j] = 0.f;
+            if (j < nB) {
+                for (int rt = 0; rt < RT; rt++) {
+                    const float yh = v[(rt * MT + j) * 64 + lane], yl = v[(rt * MT + j) * 64 + 32 + lane];
                     float se;
-                    two_sum(sh[j], y.x, sh[j], se);
-                    sl[j] = __fadd_rn(sl[j], __fadd_rn(se, y.y));
+                    two_sum(sh[j], yh, sh[j], se);
+                    sl[j] = __fadd_rn(sl[j], __fadd_rn(se, yl));
                 }
             }
         }
-        const float *u = reinterpret_cast<const float *>(v + RTMT);
-        float sv[kNB], sle[kNB];
+        float sv[MTT], sle[MTT];
 #pragma unroll
-        for (int j = 0; j < kNB; j++) two_sum(sh[j], sl[j], sv[j], sle[j]);
+        for (int j = 0; j < MTT; j++) two_sum(sh[j], sl[j], sv[j], sle[j]);
+        const float *u = v + yfl;  // [hl][MT][32]
 #pragma unroll
         for (int i = 0; i < kNB; i++) {
-            if (i >= nA) continue;
-            const float uh = u[i], ul = u[kNB + i];
+            const int ia = kNB * ig + i;
+            if (ia >= nA) continue;
+            const float uh = u[ia * 32 + lane], ul = u[(MT + ia) * 32 + lane];
 #pragma unroll
-            for (int j = 0; j < kNB; j++) {
+            for (int j = 0; j < MTT; j++) {
                 if (j >= nB) continue;
                 const float pr = __fmul_rn(uh, sv[j]);
                 const float pe = fmaf(uh, sle[j], fmaf(ul, sv[j], fmaf(uh, sv[j], -pr)));
@@ -807,59 +850,56 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
                 Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, pe));
             }
         }
+        __syncwarp();  // every lane has read the stage before it is refilled
+        issue(k + NS);
     }
-    cp_async_wait<0>();
-    __syncthreads();  // the staging slots become the tree's exchange area
-    // tree over the chi chunks: the upper half of the warps hands its pairs down
-    float(*red)[32][2 * kNB * kNB] = reinterpret_cast<float(*)[32][2 * kNB * kNB]>(red_smem);
+    // copies still in flight (after a wait gave up) land before the memory is reused
+    if (aborted)
+        for (int k = done; k < min(cnt, done + NS); k++) mbar_wait(&bars[k % NS], (k / NS) & 1);
+    __syncthreads();  // the staging rings become the tree's exchange area
+    float *red = reinterpret_cast<float *>(red_smem);  // [W/2][32][2 kNB MTT]
+    constexpr int ZP = 2 * kNB * MTT;
     for (int half = W / 2; half >= 1; half >>= 1) {
-        if (chunk >= half && chunk < 2 * half) {
+        if (w >= half && w < 2 * half) {
 #pragma unroll
             for (int i = 0; i < kNB; i++)
 #pragma unroll
-                for (int j = 0; j < kNB; j++) {
-                    red[chunk - half][lane][2 * (i * kNB + j)] = Zh[i][j];
-                    red[chunk - half][lane][2 * (i * kNB + j) + 1] = Zl[i][j];
+                for (int j = 0; j < MTT; j++) {
+                    red[((w - half) * 32 + lane) * ZP + 2 * (i * MTT + j)] = Zh[i][j];
+                    red[((w - half) * 32 + lane) * ZP + 2 * (i * MTT + j) + 1] = Zl[i][j];
                 }
         }
         __syncthreads();
-        if (chunk < half) {
+        if (w < half) {
 #pragma unroll
             for (int i = 0; i < kNB; i++)
 #pragma unroll
-                for (int j = 0; j < kNB; j++) {
+                for (int j = 0; j < MTT; j++) {
                     float se;
-                    two_sum(Zh[i][j], red[chunk][lane][2 * (i * kNB + j)], Zh[i][j], se);
-                    Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, red[chunk][lane][2 * (i * kNB + j) + 1]));
+                    two_sum(Zh[i][j], red[(w * 32 + lane) * ZP + 2 * (i * MTT + j)], Zh[i][j], se);
+                    Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, red[(w * 32 + lane) * ZP + 2 * (i * MTT + j) + 1]));
                 }
         }
         __syncthreads();
     }
-    if (chunk != 0 || !active) return;
+    if (w != 0 || !rq || col < 0) return;
     const double pf = pref[t * L + e];
     const int ngg = ng * (ng + 1) / 2, ngs = ng * ns;
 #pragma unroll
     for (int i = 0; i < kNB; i++) {
+        const int ia = kNB * ig + i;
 #pragma unroll
-        for (int j = 0; j < kNB; j++) {
-            if (i >= nA || j >= nB) continue;
+        for (int j = 0; j < MTT; j++) {
+            if (ia >= nA || j >= nB) continue;
             int p;
-            if (t == 0) { if (i > j) continue; p = i * ng - i * (i - 1) / 2 + (j - i); }
-            else if (t == 1) p = ngg + i * ns + j;
-            else { if (i > j) continue; p = ngg + ngs + i * ns - i * (i - 1) / 2 + (j - i); }
+            if (t == 0) { if (ia > j) continue; p = ia * ng - ia * (ia - 1) / 2 + (j - ia); }
+            else if (t == 1) p = ngg + ia * ns + j;
+            else { if (ia > j) continue; p = ngg + ngs + ia * ns - ia * (ia - 1) / 2 + (j - ia); }
             double out = pf * ((double)Zh[i][j] + (double)Zl[i][j]);
             if (rq->status) out = nan("");
             rq->cl[(size_t)p * rq->n_sel + col] = out;
         }
     }
-}
-
-// Shared memory of k_reduce_tc<W, STG>: the staging slots, at least the tree's area.
-size_t reduce_smem(int W, int STG, int RT, int MT)
-{
-    const size_t stage = (size_t)W * STG * 32 * reduce_slot_f2(RT, MT) * sizeof(float2);
-    const size_t tree = (size_t)(W / 2) * 32 * 2 * kNB * kNB * sizeof(float);
-    return stage > tree ? stage : tree;
 }
 
 // ---------------------------------------------------------------- host side
@@ -881,13 +921,14 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 3-D map over [S][rows][Kp] bf16, box {64, box_rows, S}, 128-byte swizzle.
-int make_map(CUtensorMap *m, void *base, int Kp, long long rows, int box_rows)
+// 3-D map over [S][rows][Kst] bf16, box {64, box_rows, S}, 128-byte swizzle;
+// boxes at x = 64 past Kst read zeros.
+int make_map(CUtensorMap *m, void *base, int Kst, long long rows, int box_rows)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return BLAST_EDEVICE;
-    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)kS};
-    cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+    cuuint64_t dims[3] = {(cuuint64_t)Kst, (cuuint64_t)rows, (cuuint64_t)kS};
+    cuuint64_t strides[2] = {(cuuint64_t)Kst * 2, (cuuint64_t)rows * Kst * 2};
     cuuint32_t box[3] = {(cuuint32_t)kKC, (cuuint32_t)box_rows, (cuuint32_t)kS};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
@@ -900,29 +941,47 @@ int make_map(CUtensorMap *m, void *base, int Kp, long long rows, int box_rows)
     return BLAST_OK;
 }
 
-// Work space of one tensor-core call: coefficient slices, scales, transposed U.
-size_t tc_ws_bytes(const blast_plan *p, int Bpad)
-{
-    return (size_t)kS * Bpad * p->Kp * 2 + (size_t)Bpad * 4 +
-           2 * (size_t)(p->max_clust + p->max_lens) * p->X * Bpad * 4 + 256;
-}
+int bpad_of(int n) { return (n + kM - 1) / kM * kM; }
 
-size_t tc_smem_bytes()
+// Work space of one tensor-core call: coefficient slices, scales, chi weights U.
+size_t tc_a_bytes(const blast_plan *p, int Bpad) { return ((size_t)kS * Bpad * p->Kst * 2 + 255) / 256 * 256; }
+size_t tc_sa_bytes(int Bpad) { return ((size_t)Bpad * 4 + 255) / 256 * 256; }
+size_t tc_u_bytes(const blast_plan *p, int Bpad) { return (size_t)Bpad * p->X * 4 * p->max_tr * 4; }
+
+template <int KC, int NG>
+int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const TcArgs &args, cudaStream_t s)
 {
-    return 1024 + kStages * kBStageBytes + kCtrlBytes + 2 * (kEP - 1) * 2 * kNB * kM * sizeof(float) +
-           kNB * (kHC / 2) * 128 * kEP * sizeof(f32x2);
+    using C = TcCfg<KC, NG>;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    const int units = args.nbt * args.nqt;
+    int grid = sms / args.nbt * args.nbt;
+    if (grid > units) grid = units;
+    if (grid < args.nbt) grid = args.nbt;
+    BL_CUDA(cudaFuncSetAttribute(k_contract_tc<KC, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem));
+    k_contract_tc<KC, NG><<<grid, kThreads, C::kSmem, s>>>(mapB, args);
+    BL_CUDA(cudaGetLastError());
+    return BLAST_OK;
 }
 
 }  // namespace
 
+// Tensor-core path limits: Chebyshev order <= 96 (coefficient slices and two
+// accumulator buffers fit the 512 TMEM columns), n_R a multiple of 32 (whole
+// R-tiles), at most 10 tracers of each kind (two groups of five).
 bool tc_supported(const blast_plan *p)
 {
-    return p->Kp == kKC && p->Rn % kQT == 0 && p->max_clust <= kNB && p->max_lens <= kNB;
+    return p->Kmma <= 96 && p->Rn % kQT == 0 && p->max_clust <= 2 * kNB && p->max_lens <= 2 * kNB;
+}
+
+size_t tc_y_bytes(const blast_plan *p, int n, int n_esel)
+{
+    return (size_t)3 * n_esel * p->X * bpad_of(n) * (p->Rn / kQT) * p->max_tr * 2 * 4;
 }
 
 int launch_basis_slices(blast_plan *p, cudaStream_t s)
 {
-    k_basis_slices<<<152 * 8, 256, 0, s>>>(p->T64, p->L, p->N, p->Q, p->Kp, p->Tsl, p->scT);
+    k_basis_slices<<<152 * 8, 256, 0, s>>>(p->T64, p->L, p->N, p->Q, p->Kst, p->Tsl, p->scT);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
 }
@@ -932,19 +991,17 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
 {
     if (!tc_supported(p)) return BLAST_EINVAL;
     Workspace &ws = p->ws;
-    const int Bpad = (n + kM - 1) / kM * kM;
+    const int Bpad = bpad_of(n);
     int rc;
-    const int ntr_max = p->max_clust + p->max_lens;
-    if ((rc = ws.tc.ensure(tc_ws_bytes(p, Bpad)))) return rc;
+    if ((rc = ws.tc.ensure(tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad) + tc_u_bytes(p, Bpad)))) return rc;
     uint16_t *A = ws.tc.as<uint16_t>();
-    float *sa = reinterpret_cast<float *>(A + (size_t)kS * Bpad * p->Kp);
-    float *UT = sa + Bpad;
-    float *UTl = UT + (size_t)ntr_max * p->X * Bpad;
-    k_coef_slices<<<Bpad / 8, 256, 0, s>>>(dreq, n, p->N, p->Kp, Bpad, A, sa, p->X, ntr_max, UT, UTl);
+    float *sa = reinterpret_cast<float *>(ws.tc.as<char>() + tc_a_bytes(p, Bpad));
+    float *U = reinterpret_cast<float *>(ws.tc.as<char>() + tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad));
+    k_coef_slices<<<Bpad / 8, 256, 0, s>>>(dreq, n, p->N, p->Kst, Bpad, A, sa, p->X, p->max_tr, U);
     BL_CUDA(cudaGetLastError());
 
     CUtensorMap mapB;
-    if ((rc = make_map(&mapB, p->Tsl, p->Kp, (long long)3 * p->L * p->Q, kQT))) return rc;
+    if ((rc = make_map(&mapB, p->Tsl, p->Kst, (long long)3 * p->L * p->Q, kQT))) return rc;
     TcArgs args;
     args.reqs = dreq;
     args.n = n;
@@ -957,45 +1014,47 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     args.Rn = p->Rn;
     args.RT = p->Rn / kQT;
     args.MT = p->max_tr;
+    args.X = p->X;
+    args.Kst = p->Kst;
+    args.Kmma = p->Kmma;
     args.esel = d_esel;
     args.scT = p->scT;
     args.sa = sa;
     args.A = A;
     args.Y = (float *)ypart;
     args.err = p->d_err;
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    int units = args.nbt * args.nqt;
-    int grid = sms / args.nbt * args.nbt;
-    if (grid > units) grid = units;
-    if (grid < args.nbt) grid = args.nbt;
-    size_t smem = tc_smem_bytes();
-    BL_CUDA(cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_contract_tc<<<grid, kThreads, smem, s>>>(mapB, args);
-    BL_CUDA(cudaGetLastError());
-    return BLAST_OK;
+    const bool two_chunks = p->Kst > kKC, two_groups = p->max_tr > kNB;
+    if (!two_chunks && !two_groups) return launch_contract_inst<1, 1>(p, mapB, args, s);
+    if (!two_chunks) return launch_contract_inst<1, 2>(p, mapB, args, s);
+    if (!two_groups) return launch_contract_inst<2, 1>(p, mapB, args, s);
+    return launch_contract_inst<2, 2>(p, mapB, args, s);
 }
 
 int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int n_esel, const void *ypart,
                      cudaStream_t s)
 {
-    const int Bpad = (n + kM - 1) / kM * kM;
-    const float *UT = reinterpret_cast<const float *>(p->ws.tc.as<uint16_t>() + (size_t)kS * Bpad * p->Kp) + Bpad;
-    const float *UTl = UT + (size_t)(p->max_clust + p->max_lens) * p->X * Bpad;
+    const int Bpad = bpad_of(n);
+    const float *U =
+        reinterpret_cast<const float *>(p->ws.tc.as<char>() + tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad));
     const int RT = p->Rn / kQT, MT = p->max_tr;
-    dim3 grid((n + 31) / 32, n_esel, 3);
-    constexpr size_t kSmemMax = 220 * 1024;
-    if (reduce_smem(8, 2, RT, MT) <= kSmemMax / 2) {  // 8 chi chunks, 2 stages, two blocks per SM
-        const int smem = (int)reduce_smem(8, 2, RT, MT);
-        BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_reduce_tc<8, 2><<<grid, 32 * 8, smem, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel,
-                                                     n_esel, RT, MT, p->d_pref);
-    } else {  // long R-tile rows (n_R up to 512): 4 chunks, 2 stages
-        const int smem = (int)reduce_smem(4, 2, RT, MT);
-        if ((size_t)smem > kSmemMax) return BLAST_EINVAL;
-        BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_reduce_tc<4, 2><<<grid, 32 * 4, smem, s>>>(dreq, (const float *)ypart, UT, UTl, n, Bpad, p->X, p->L, d_esel,
-                                                     n_esel, RT, MT, p->d_pref);
+    const size_t stage = ((size_t)RT * MT * 64 + 2 * MT * 32) * 4;
+    // 4 warps (chi chunks), 2 for large stages, with as many stages each as fit
+    // two blocks per SM
+    const int W = stage > 8192 ? 2 : 4;
+    int NS = (int)((110 * 1024) / (W * (stage + 8)));
+    if (NS > 6) NS = 6;
+    if (NS < 1) return BLAST_EINVAL;
+    const size_t smem = (size_t)W * NS * (stage + 8);
+    const bool big = MT > kNB;
+    dim3 grid(Bpad / 32, n_esel, big ? 6 : 3);
+    if (big) {
+        BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<2 * kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_reduce_tc<2 * kNB><<<grid, 32 * W, smem, s>>>(dreq, (const float *)ypart, U, n, p->X, p->L, d_esel,
+                                                       n_esel, RT, MT, Bpad / 32, NS, p->d_pref, p->d_err);
+    } else {
+        BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_reduce_tc<kNB><<<grid, 32 * W, smem, s>>>(dreq, (const float *)ypart, U, n, p->X, p->L, d_esel, n_esel,
+                                                    RT, MT, Bpad / 32, NS, p->d_pref, p->d_err);
     }
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;

@@ -541,7 +541,7 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
     int rc = stage_batch(p, n, reqs, prec, outs, out_mem_space, s, &dreq, &d_esel, &n_esel, hreq, direct_out);
     if (rc) return rc;
     if (use_tc) {
-        const size_t ybytes = (size_t)n * 3 * n_esel * p->X * (p->Rn / 32) * 2 * p->max_tr * 4;
+        const size_t ybytes = tc_y_bytes(p, n, n_esel);
         if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
         if ((rc = prof_launch(p, BLAST_K_CONTRACT_TC, s, [&] {
                  return launch_contract_tc(p, dreq, n, d_esel, n_esel, p->ws.ypart.p, s);

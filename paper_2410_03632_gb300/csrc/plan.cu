@@ -202,7 +202,8 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
     p->max_clust = d->max_clust; p->max_lens = d->max_lens;
     p->max_tr = d->max_clust > d->max_lens ? d->max_clust : d->max_lens;
     p->device = d->device;
-    p->Kp = (p->N + 63) / 64 * 64;
+    p->Kmma = (p->N + 15) / 16 * 16;
+    p->Kst = p->Kmma > 64 ? p->Kmma : 64;
 
     // chi: uniform nodes, composite Simpson (+ 3/8 panel on the last three
     // intervals when the number of intervals is odd)
@@ -326,8 +327,8 @@ int plan_alloc_basis(blast_plan *p, unsigned mask)
         if (cudaMalloc(&p->T32, n64 * sizeof(float)) != cudaSuccess) { cudaGetLastError(); p->T32 = nullptr; return BLAST_ENOMEM; }
     }
     if ((mask & BLAST_BASIS_BF16S) && tc_supported(p) && !p->Tsl) {
-        if (cudaMalloc(&p->Tsl, ncol * p->Kp * 2 * BLAST_TC_SLICES) != cudaSuccess) { cudaGetLastError(); p->Tsl = nullptr; return BLAST_ENOMEM; }
-        if (cudaMalloc(&p->scT, ncol * sizeof(float)) != cudaSuccess) { cudaGetLastError(); p->scT = nullptr; return BLAST_ENOMEM; }
+        if (cudaMalloc(&p->Tsl, ncol * p->Kst * 2 * BLAST_TC_SLICES) != cudaSuccess) { cudaGetLastError(); p->Tsl = nullptr; return BLAST_ENOMEM; }
+        if (cudaMalloc(&p->scT, ncol / 32 * sizeof(float)) != cudaSuccess) { cudaGetLastError(); p->scT = nullptr; return BLAST_ENOMEM; }
     }
     return BLAST_OK;
 }

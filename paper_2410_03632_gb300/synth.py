@@ -231,6 +231,14 @@ def plan_spec(name: str) -> PlanSpec:
         # oracle's basis finishes in about a minute
         return PlanSpec(np.array([2, 300, 600, 1000], np.int32), 9, 26.0, 4100.0, 64, 0.2, 1.8, 64,
                         1e-4, 10.0, 1, kquad_points(1e-4, 10.0, 4100.0, 1.8), 5, 5)
+    elif name == "tcg":
+        # tensor-core shapes with two groups of tracer weights (7 + 6 tracers), order 40
+        return PlanSpec(ell_list(6, 2, 250), 13, 40.0, 2400.0, 64, 0.2, 1.8, 40, 1e-4, 1.0, 1,
+                        kquad_points(1e-4, 1.0, 2400.0, 1.8), 7, 6)
+    elif name == "tck":
+        # tensor-core shapes with the order past 64 (two K chunks, four TMEM levels), order 80
+        return PlanSpec(ell_list(6, 2, 250), 13, 40.0, 2400.0, 64, 0.2, 1.8, 80, 1e-4, 1.0, 1,
+                        kquad_points(1e-4, 1.0, 2400.0, 1.8), 3, 2)
     elif name == "tc":
         # tensor-core path shapes: n_R a multiple of 32, n_cheb <= 64, <= 5 tracers per kind
         return PlanSpec(ell_list(9, 2, 300), 21, 40.0, 2400.0, 64, 0.2, 1.8, 40, 1e-4, 1.0, 1,
@@ -244,14 +252,15 @@ def plan_spec(name: str) -> PlanSpec:
 def config_request(name: str, chi, R, idx: int = 0) -> Request:
     """The seeded request of a workload: seed 1000 + config + 7919 idx."""
     spec = plan_spec(name)
-    cfg = {"c0": 0, "c1": 1, "c2": 2, "tiny": 10, "small": 11, "tc": 12, "c2s": 13, "c1hi": 1}[name]
+    cfg = {"c0": 0, "c1": 1, "c2": 2, "tiny": 10, "small": 11, "tc": 12, "c2s": 13, "c1hi": 1, "tcg": 14,
+           "tck": 15}[name]
     rng = np.random.default_rng(1000 + cfg + 7919 * idx)
     ng, ns = spec.max_clust, spec.max_lens
     zb = {}
     if name == "tiny":   # grid reaches z ~ 0.33
         zb = dict(mus_g=np.array([0.1, 0.2]), sig_g=np.array([0.02, 0.04]),
                   mus_s=np.array([0.22, 0.3]), sig_s=np.array([0.03, 0.05]))
-    elif name in ("small", "tc"):  # grid reaches z ~ 1.1
+    elif name in ("small", "tc", "tcg", "tck"):  # grid reaches z ~ 1.1
         zb = dict(mus_g=np.linspace(0.2, 0.7, ng), sig_g=np.linspace(0.05, 0.1, ng),
                   mus_s=np.linspace(0.5, 0.8, ns), sig_s=np.linspace(0.08, 0.12, ns))
     if name == "c0" and idx == 0:

@@ -84,6 +84,38 @@ def test_tc_two_ragged_cosmology_tiles(tc_case):
     assert np.array_equal(outs[0], outs[125]) and np.array_equal(outs[4], outs[129])
 
 
+@pytest.mark.parametrize("name", ["tcg", "tck"])
+def test_tc_other_kernel_shapes(name):
+    """The instances with tracer weights in two groups of five (7 + 6 tracers,
+    weights of tracers 5.. in shared memory) and with the order past 64 (two K
+    chunks per stage, four TMEM levels, the last holding slice levels 3 and 4)
+    against the oracle, with uneven tracer counts and ell subsets."""
+    spec = synth.plan_spec(name)
+    g = orc.Grid(spec.ells, spec.n_chi, spec.chi_min, spec.chi_max, spec.n_R, spec.R_min, spec.R_max,
+                 spec.n_cheb, spec.k_min, spec.k_max, spec.n_kquad, spec.k_map)
+    T = g.basis()
+    plan = bl.Plan(spec)
+    try:
+        plan.precompute(bl.BASIS_ALL)
+        mc, ml = spec.max_clust, spec.max_lens
+        counts = [(mc, ml), (mc - 1, ml), (1, ml - 1), (mc, 0), (0, ml)]
+        L = spec.ells.size
+        sels = [None, [0, L - 1], None, list(range(1, L, 2)), None]
+        rqs = [subset_request(synth.config_request(name, g.chi, g.R, i), ng, ns, mc)
+               for i, (ng, ns) in enumerate(counts)]
+        outs = plan.cl_batch(rqs, bl.BLAST_BF16S, sels)
+        worst = 0.0
+        for rq, s, C in zip(rqs, sels, outs):
+            Co = oracle_cl(g, T, rq, s)
+            assert C.shape == Co.shape
+            worst = max(worst, float(np.max(eij(C, Co, rq.n_clust, rq.n_lens))))
+            assert np.array_equal(plan.cl(rq, bl.BLAST_BF16S, ell_sel=s), C)
+        print(f"\n{name}: worst e_ij against the oracle {worst:.3e}")
+        assert worst < TOL
+    finally:
+        plan.close()
+
+
 def test_tc_rejects_unsupported_plan():
     spec = synth.plan_spec("tiny")  # n_R = 10 is not a multiple of 32
     plan = bl.Plan(spec)
