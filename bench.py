@@ -361,9 +361,11 @@ def run_blast(args):
     kern = {}
     rms, rl = prof_main["reduce"]
     if rl and have_tc:
-        ntr_max = plan.max_clust + plan.max_lens
-        red_bytes = (B * 3 * L * X * (plan.Rn // 32) * 5 * 8 + ntr_max * X * (-(-B // 128) * 128) * 8
-                     + B * P * L * 8)
+        MT = max(spec.max_clust, spec.max_lens)
+        Bp = -(-B // 128) * 128
+        # R-tile partial pairs of every padded cosmology, chi weights (hi, lo) of the
+        # A-side kind per type, and the C_l written
+        red_bytes = Bp * 3 * L * X * (plan.Rn // 32) * MT * 8 + 3 * Bp * X * MT * 8 + B * P * L * 8
         gbs = red_bytes / (rms / rl * 1e-3) / 1e9
         kern["reduce"] = {"bound": "hbm", "bytes_per_launch": red_bytes, "achieved": gbs,
                           "peak": peaks.get("hbm_gbs"), "frac": gbs / peaks.get("hbm_gbs", 6800.0),

@@ -54,8 +54,8 @@ constexpr int kS = BLAST_TC_SLICES;       // slices per operand
 constexpr int kQT = 32;                   // chi-R nodes per tile (MMA N)
 constexpr int kM = 128;                   // cosmologies per tile (MMA M)
 constexpr int kKC = 64;                   // K elements per 128-byte swizzle row (one TMA box)
-constexpr int kEP = 2;                    // epilogue warps per TMEM lane quadrant
-constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 8 epilogue warps
+constexpr int kEP = 4;                    // epilogue warps per TMEM lane quadrant
+constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 16 epilogue warps
 constexpr int kHC = kQT / kEP;            // columns per epilogue thread
 constexpr int kCS = 4;                    // columns per TMEM load step
 constexpr int kNB = 5;                    // tracers per weight group
@@ -63,19 +63,19 @@ constexpr int kNBUF = 2;                  // TMEM accumulator buffers
 constexpr uint32_t kBSliceBytes = kQT * 128;  // 32 rows x 64 bf16
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kCtrlBytes = 256;          // mbarriers, TMEM address, abort flag
+constexpr uint32_t kEselBytes = 4 * BLAST_MAX_ELL;  // selected ells
 constexpr long long kWaitLimit = 4000000000LL;  // clock cycles (about 2 s)
 constexpr uint32_t kSuspendNs = 1000000;        // longest suspension of one phase test
 
 // Compile-time shape of one kernel instance: KC 64-wide K chunks per stage
-// (1: order <= 64, 2: order <= 96), NG groups of five tracers per kind.
-template <int KC, int NG> struct TcCfg {
+// (1: order <= 64, 2: order <= 96).
+template <int KC> struct TcCfg {
     static constexpr int LV = KC == 1 ? 5 : 4;              // TMEM accumulator levels
-    static constexpr int kStages = KC == 1 ? (NG == 1 ? 8 : 6) : (NG == 1 ? 4 : 3);
+    static constexpr int kStages = KC == 1 ? 8 : 4;  // 160 KB of basis slices in flight
     static constexpr uint32_t kStageBytes = KC * kS * kBSliceBytes;
     static constexpr uint32_t kACol = kNBUF * LV * kQT;     // TMEM column of the coefficient slices
-    static constexpr int kYbufFloats = 2 * 4 * NG * kNB * 64; // [parity][quadrant][tracer][hi, lo][lane]
-    static constexpr size_t kVsmBytes = NG == 2 ? (size_t)kNB * (kHC / 2) * 128 * kEP * 8 : 0;
-    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kCtrlBytes + kYbufFloats * 4 + kVsmBytes;
+    static constexpr int kYbufFloats = 2 * 4 * (kEP - 1) * kNB * 64;  // [parity][quadrant][part-1][tracer][hi, lo][lane]
+    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kCtrlBytes + kEselBytes + kYbufFloats * 4;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -406,7 +406,7 @@ __global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q
 // ---------------------------------------------------------------- main kernel
 struct TcArgs {
     const ReqDev *reqs;
-    int n, Bpad, nbt, nqt, n_esel, L, Q, Rn, RT, MT, X, Kst, Kmma;
+    int n, Bpad, nbt, ngr, nqt, n_esel, L, Q, Rn, RT, MT, X, Kst, Kmma;
     const int *esel;
     const float *scT;    // [3][L][Q / kQT] one scale per tile
     const float *sa;     // [Bpad]
@@ -415,14 +415,24 @@ struct TcArgs {
     int *err;            // host-mapped error word
 };
 
-template <int KC, int NG>
+// Work units: (cosmology tile, group of five B-side tracers, 32-column q
+// tile).  A CTA keeps its cosmology tile (the grid is a multiple of nbt), so
+// the coefficient slices stay in TMEM for the whole launch; each unit runs
+// the 3 n_esel (type, ell) tiles of its q tile.
+__device__ __forceinline__ void unit_decode(const TcArgs &a, int u, int &grp, int &q0)
+{
+    grp = (u / a.nbt) % a.ngr;
+    q0 = (u / (a.nbt * a.ngr)) * kQT;
+}
+
+template <int KC>
 __global__ void __launch_bounds__(kThreads, 1)
 k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
 {
-    using C = TcCfg<KC, NG>;
+    using C = TcCfg<KC>;
     constexpr int LV = C::LV;
     constexpr int kStages = C::kStages;
-    constexpr int NGB = NG * kNB;  // tracers per kind this instance serves
+    constexpr int NGB = kNB;  // B-side tracers of one unit
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -432,12 +442,13 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     uint64_t *tfull = aready + 1, *tempty = tfull + kNBUF, *mdone = tempty + kNBUF;
     uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    float *ybuf = (float *)((unsigned char *)bars + kCtrlBytes);       // [2][4][NGB][2][32] column-half hand-over
-    f32x2 *vsm = (f32x2 *)(ybuf + C::kYbufFloats);                    // [kNB][kHC/2][256] weights of tracers 5..9
+    int *s_esel = (int *)((unsigned char *)bars + kCtrlBytes);         // selected ells
+    float *ybuf = (float *)((unsigned char *)s_esel + kEselBytes);     // [2][4][kEP-1][NGB][2][32] column-part hand-over
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int btile = blockIdx.x % args.nbt;
     const int n_iter_unit = 3 * args.n_esel;
+    const int n_units = args.nbt * args.ngr * args.nqt;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; i++) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
@@ -447,6 +458,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int i = threadIdx.x; i < args.n_esel; i += blockDim.x) s_esel[i] = args.esel[i];
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols));
@@ -461,8 +473,9 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         // ------------------------------------------------ TMA producer (whole warp waits, one lane issues)
         uint32_t g = 0;
         bool ok = true;
-        for (int u = blockIdx.x; ok && u < args.nbt * args.nqt; u += gridDim.x) {
-            const int q0 = (u / args.nbt) * kQT;
+        for (int u = blockIdx.x; ok && u < n_units; u += gridDim.x) {
+            int grp, q0;
+            unit_decode(args, u, grp, q0);
             for (int it = 0; it < n_iter_unit; it++, g++) {
                 const int st = g % kStages;
                 const uint32_t ph = (g / kStages) & 1;
@@ -473,7 +486,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                     break;
                 }
                 if (elect_one()) {
-                    const int t = it / args.n_esel, e = args.esel[it % args.n_esel];
+                    const int t = it / args.n_esel, e = s_esel[it % args.n_esel];
                     const int row = (t * args.L + e) * args.Q + q0;
                     mbar_expect_tx(&full[st], C::kStageBytes);
 #pragma unroll
@@ -499,7 +512,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         const int nk = args.Kmma / 16;        // K steps of 16
         const uint32_t acol = args.Kmma / 2;  // TMEM columns per coefficient slice
         uint32_t g = 0;
-        for (int u = blockIdx.x; ok && u < args.nbt * args.nqt; u += gridDim.x) {
+        for (int u = blockIdx.x; ok && u < n_units; u += gridDim.x) {
             for (int it = 0; it < n_iter_unit; it++, g++) {
                 const int st = g % kStages;
                 const uint32_t ph = (g / kStages) & 1;
@@ -587,18 +600,21 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         uint32_t g = 0;
         bool dead = false;
         f32x2 vr[kNB][kHC / 2];  // quadrature weights (times 2^ea) of tracers 0..4 of the B-side kind
-        for (int u = blockIdx.x; u < args.nbt * args.nqt; u += gridDim.x) {
-            const int q0 = (u / args.nbt) * kQT;
+        for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+            int grp, q0;
+            unit_decode(args, u, grp, q0);
             const int a = q0 / args.Rn, rt = (q0 % args.Rn) / kQT;
             for (int t = 0; t < 3; t++) {
                 const int offB = (t == 0) ? 0 : ng, nB = (t == 0) ? ng : ns;
                 if (t < 2) {
-                    // weights of the B-side kind: clustering for gg, lensing for gs and ss
+                    // weights of the B-side kind (clustering for gg, lensing for gs and
+                    // ss), tracers 5 grp .. 5 grp + 4 of it
 #pragma unroll
                     for (int j = 0; j < kNB; j++) {
+                        const int jj = kNB * grp + j;
                         const float4 *src =
-                            (valid && j < nB)
-                                ? reinterpret_cast<const float4 *>(rq->V32 + (size_t)(offB + j) * args.Q + q0 + cb)
+                            (valid && jj < nB)
+                                ? reinterpret_cast<const float4 *>(rq->V32 + (size_t)(offB + jj) * args.Q + q0 + cb)
                                 : nullptr;
 #pragma unroll
                         for (int c = 0; c < kHC / 4; c++) {
@@ -607,24 +623,13 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                             vr[j][2 * c + 1] = pk2(v.z * sa, v.w * sa);
                         }
                     }
-                    if (NG == 2) {  // tracers 5..9 in this thread's own shared-memory slots
-                        for (int j = 0; j < kNB; j++) {
-                            const float4 *src = (valid && kNB + j < nB)
-                                                    ? reinterpret_cast<const float4 *>(
-                                                          rq->V32 + (size_t)(offB + kNB + j) * args.Q + q0 + cb)
-                                                    : nullptr;
-#pragma unroll
-                            for (int c = 0; c < kHC / 4; c++) {
-                                const float4 v = src ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-                                vsm[(j * (kHC / 2) + 2 * c) * (128 * kEP) + tid_e] = pk2(v.x * sa, v.y * sa);
-                                vsm[(j * (kHC / 2) + 2 * c + 1) * (128 * kEP) + tid_e] = pk2(v.z * sa, v.w * sa);
-                            }
-                        }
-                    }
                 }
                 for (int es = 0; es < args.n_esel; es++, g++) {
                     const int buf = g % kNBUF;
                     const uint32_t tph = (g / kNBUF) & 1;
+                    // the tile's scale 2^(eG - 16), fetched while the MMA finishes
+                    const float tsc =
+                        (part == 0) ? args.scT[((size_t)t * args.L + s_esel[es]) * (args.Q / kQT) + q0 / kQT] : 0.f;
                     if (!dead) {
                         bool lost = *abort_flag != 0;
                         if (!lost && !mbar_wait(&tfull[buf], tph)) {
@@ -681,12 +686,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
 #pragma unroll
                                 for (int j = 0; j < NGB; j++) {
                                     const int pc = s * (kCS / 2) + h0;  // packed column pair index
-                                    f32x2 v0, v1;
-                                    if (j < kNB) { v0 = vr[j][pc]; v1 = vr[j][pc + 1]; }
-                                    else {
-                                        v0 = vsm[((j - kNB) * (kHC / 2) + pc) * (128 * kEP) + tid_e];
-                                        v1 = vsm[((j - kNB) * (kHC / 2) + pc + 1) * (128 * kEP) + tid_e];
-                                    }
+                                    const f32x2 v0 = vr[j][pc], v1 = vr[j][pc + 1];
                                     const f32x2 p0 = mul2(v0, mn0), p1 = mul2(v1, mn1);   // -fl(v m)
                                     const f32x2 e0 = fma2(v0, lo[h0], fma2(v0, m[h0], p0));  // v lo + (v m - fl(v m))
                                     const f32x2 e1 = fma2(v1, lo[h1], fma2(v1, m[h1], p1));
@@ -712,32 +712,37 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                             Sl[j] = -__fadd_rn(el, __fadd_rn(B2.x, B2.y));
                         }
                     }
-                    // the column halves meet: part 1 hands its pairs to part 0 through
+                    // the column parts meet: parts 1.. hand their pairs to part 0 through
                     // shared memory, double buffered by iteration
-                    float *yq = ybuf + ((size_t)(g & 1) * 4 + quad) * (NGB * 64);
-                    if (part == 1) {
+                    float *yq = ybuf + ((size_t)(g & 1) * 4 + quad) * ((kEP - 1) * NGB * 64);
+                    if (part > 0) {
+                        float *slot = yq + (size_t)(part - 1) * NGB * 64;
 #pragma unroll
-                        for (int j = 0; j < NGB; j++) { yq[j * 64 + lane] = Sh[j]; yq[j * 64 + 32 + lane] = Sl[j]; }
+                        for (int j = 0; j < NGB; j++) { slot[j * 64 + lane] = Sh[j]; slot[j * 64 + 32 + lane] = Sl[j]; }
                     }
                     named_bar_sync(bar_id, 32 * kEP);
                     if (part == 0 && !dead) {
 #pragma unroll
-                        for (int j = 0; j < NGB; j++) {
-                            float se;
-                            two_sum(Sh[j], yq[j * 64 + lane], Sh[j], se);
-                            Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, yq[j * 64 + 32 + lane]));
+                        for (int q = 0; q < kEP - 1; q++) {
+                            const float *slot = yq + (size_t)q * NGB * 64;
+#pragma unroll
+                            for (int j = 0; j < NGB; j++) {
+                                float se;
+                                two_sum(Sh[j], slot[j * 64 + lane], Sh[j], se);
+                                Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, slot[j * 64 + 32 + lane]));
+                            }
                         }
                         if (valid) {
-                            // the tile's scale 2^(eG - 16) (exact); the pair (hi, lo) of tracer j
-                            // at Y[t][es][a][b / 32][rt][j][hi, lo][b % 32]: a warp stores 128 bytes
-                            const float tsc =
-                                args.scT[((size_t)t * args.L + args.esel[es]) * (args.Q / kQT) + q0 / kQT];
+                            // times the tile's scale (exact); the pair (hi, lo) of tracer j at
+                            // Y[t][es][a][b / 32][rt][j][hi, lo][b % 32]: a warp stores 128 bytes
                             float *y = args.Y +
                                        (((((size_t)t * args.n_esel + es) * args.X + a) * (args.Bpad / 32) + (b >> 5)) *
                                             args.RT + rt) * (size_t)args.MT * 64 + lane;
 #pragma unroll
-                            for (int j = 0; j < NGB; j++)
-                                if (j < args.MT) { y[j * 64] = Sh[j] * tsc; y[j * 64 + 32] = Sl[j] * tsc; }
+                            for (int j = 0; j < NGB; j++) {
+                                const int jj = kNB * grp + j;
+                                if (jj < args.MT) { y[jj * 64] = Sh[j] * tsc; y[jj * 64 + 32] = Sl[j] * tsc; }
+                            }
                         }
                     }
                 }
@@ -823,6 +828,7 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
             sh[j] = 0.f;
             sl[j] = 0.f;
             if (j < nB) {
+#pragma unroll 2
                 for (int rt = 0; rt < RT; rt++) {
                     const float yh = v[(rt * MT + j) * 64 + lane], yl = v[(rt * MT + j) * 64 + 32 + lane];
                     float se;
@@ -948,18 +954,18 @@ size_t tc_a_bytes(const blast_plan *p, int Bpad) { return ((size_t)kS * Bpad * p
 size_t tc_sa_bytes(int Bpad) { return ((size_t)Bpad * 4 + 255) / 256 * 256; }
 size_t tc_u_bytes(const blast_plan *p, int Bpad) { return (size_t)Bpad * p->X * 4 * p->max_tr * 4; }
 
-template <int KC, int NG>
+template <int KC>
 int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const TcArgs &args, cudaStream_t s)
 {
-    using C = TcCfg<KC, NG>;
+    using C = TcCfg<KC>;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    const int units = args.nbt * args.nqt;
+    const int units = args.nbt * args.ngr * args.nqt;
     int grid = sms / args.nbt * args.nbt;
     if (grid > units) grid = units;
     if (grid < args.nbt) grid = args.nbt;
-    BL_CUDA(cudaFuncSetAttribute(k_contract_tc<KC, NG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem));
-    k_contract_tc<KC, NG><<<grid, kThreads, C::kSmem, s>>>(mapB, args);
+    BL_CUDA(cudaFuncSetAttribute(k_contract_tc<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem));
+    k_contract_tc<KC><<<grid, kThreads, C::kSmem, s>>>(mapB, args);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
 }
@@ -1023,11 +1029,9 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     args.A = A;
     args.Y = (float *)ypart;
     args.err = p->d_err;
-    const bool two_chunks = p->Kst > kKC, two_groups = p->max_tr > kNB;
-    if (!two_chunks && !two_groups) return launch_contract_inst<1, 1>(p, mapB, args, s);
-    if (!two_chunks) return launch_contract_inst<1, 2>(p, mapB, args, s);
-    if (!two_groups) return launch_contract_inst<2, 1>(p, mapB, args, s);
-    return launch_contract_inst<2, 2>(p, mapB, args, s);
+    args.ngr = (p->max_tr + kNB - 1) / kNB;
+    if (p->Kst > kKC) return launch_contract_inst<2>(p, mapB, args, s);
+    return launch_contract_inst<1>(p, mapB, args, s);
 }
 
 int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int n_esel, const void *ypart,
@@ -1038,11 +1042,11 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
         reinterpret_cast<const float *>(p->ws.tc.as<char>() + tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad));
     const int RT = p->Rn / kQT, MT = p->max_tr;
     const size_t stage = ((size_t)RT * MT * 64 + 2 * MT * 32) * 4;
-    // 4 warps (chi chunks), 2 for large stages, with as many stages each as fit
+    // 8 warps (chi chunks), 2 for large stages, with as many stages each as fit
     // two blocks per SM
-    const int W = stage > 8192 ? 2 : 4;
+    const int W = stage > 8192 ? 2 : 8;
     int NS = (int)((110 * 1024) / (W * (stage + 8)));
-    if (NS > 6) NS = 6;
+    if (NS > 4) NS = 4;
     if (NS < 1) return BLAST_EINVAL;
     const size_t smem = (size_t)W * NS * (stage + 8);
     const bool big = MT > kNB;

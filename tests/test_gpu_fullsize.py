@@ -49,10 +49,11 @@ def test_benchmark_grid_sampled_at_ell_2():
         To = g.basis(ell_subset=g.ells[:1])                     # [3][1][N][Q], l = 2
         Tg = plan.basis()[:, :1]
         scale = np.max(np.abs(To), axis=-1, keepdims=True)
-        # both sides sum 65 537 oscillating FP64 terms in different orders (the
-        # oracle compensated): sqrt(65537) x 1.1e-16 x a cancellation of up to ~1e3
-        # is ~3e-11 of the row maximum (measured 4.0e-11)
-        assert np.max(np.abs(Tg - To) / np.where(scale > 0, scale, 1.0)) < 1e-10
+        # the integrand oscillates as j_l(k chi) with k chi up to ~7e4, so the two
+        # sides agree this well only because their nodes are the same IEEE values
+        db = float(np.max(np.abs(Tg - To) / np.where(scale > 0, scale, 1.0)))
+        print(f"\nbenchmark grid, l = 2: device basis vs oracle {db:.3e} of the row maximum")
+        assert db < 1e-11
         chi, R, _ = plan.nodes()
         rqs = [synth.config_request("c1", chi, R, 1 + i) for i in range(8)]
         c64 = plan.cl_batch(rqs, bl.BLAST_FP64)

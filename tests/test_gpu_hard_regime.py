@@ -15,7 +15,8 @@ Two comparisons, element by element over every spectrum and ell:
       five-slice path within 1e-4 of the oracle's C_l;
   P3  the library with its own device-computed basis, end to end: the
       five-slice path within 1e-4; FP64 within the bar that the two bases'
-      agreement allows (stated below).
+      agreement allows: the device basis within 1e-11 of the oracle's row
+      maximum, FP64 C_l within 1e-10.
 e_ij = |dC_ij| / sqrt(C_ii C_jj) (auto-spectrum normalisation).
 """
 import numpy as np
@@ -117,6 +118,6 @@ def test_p3_device_basis(hard):
     wtc = max(float(np.max(eij(b, o, 5, 5))) for b, o in zip(ctc, Co))
     print(f"\nP3 (device basis): basis vs oracle {db:.3e} of row max; FP64 C_l {w64:.3e}; "
           f"BF16 five-slice {wtc:.3e}")
-    assert db < 1e-10
+    assert db < 1e-11
     assert wtc < 1e-4
-    assert w64 < 1e-6
+    assert w64 < 1e-10
