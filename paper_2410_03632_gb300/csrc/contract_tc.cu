@@ -530,20 +530,23 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                 const uint32_t dbase = tm + buf * (LV * kQT);
                 const uint64_t bbase = sdesc(b0 + st * C::kStageBytes);
                 if (elect_one()) {
+                    // Consecutive MMAs into one accumulator wait for each other, so the
+                    // issue order interleaves the levels: per K step, rounds r = 0..4 of
+                    // the slice pairs (p = r, q = k - r) over levels k = 4 .. 0, so that
+                    // an accumulator is hit again only after the other levels had a turn.
+                    uint32_t started = 0;  // levels already written in this tile
+                    for (int kk = 0; kk < nk; kk++) {
+                        const uint32_t koff = (kk >> 2) * (kS * kBSliceBytes) + (kk & 3) * 32;
 #pragma unroll
-                    for (int lev = 0; lev < LV; lev++) {
-                        uint32_t acc = 0;
+                        for (int r = 0; r < kS; r++) {
 #pragma unroll
-                        for (int p = 0; p < kS; p++) {
-#pragma unroll
-                            for (int q = 0; q < kS - p; q++) {
-                                if ((p + q < LV - 1 ? p + q : LV - 1) != lev) continue;
-                                for (int kk = 0; kk < nk; kk++) {
-                                    const uint32_t boff = (kk >> 2) * (kS * kBSliceBytes) + q * kBSliceBytes + (kk & 3) * 32;
-                                    umma_ts(dbase + lev * kQT, tm + C::kACol + p * acol + kk * 8,
-                                            bbase + (uint64_t)(boff >> 4), acc);
-                                    acc = 1;
-                                }
+                            for (int k = kS - 1; k >= r; k--) {
+                                const int p = r, q = k - r;
+                                const int lev = k < LV - 1 ? k : LV - 1;
+                                const uint32_t boff = koff + q * kBSliceBytes;
+                                umma_ts(dbase + lev * kQT, tm + C::kACol + p * acol + kk * 8,
+                                        bbase + (uint64_t)(boff >> 4), (started >> lev) & 1u);
+                                started |= 1u << lev;
                             }
                         }
                     }
