@@ -54,8 +54,8 @@ constexpr int kS = BLAST_TC_SLICES;       // slices per operand
 constexpr int kQT = 32;                   // chi-R nodes per tile (MMA N)
 constexpr int kM = 128;                   // cosmologies per tile (MMA M)
 constexpr int kKC = 64;                   // K elements per 128-byte swizzle row (one TMA box)
-constexpr int kEP = 4;                    // epilogue warps per TMEM lane quadrant
-constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 16 epilogue warps
+constexpr int kEP = 2;                    // epilogue warps per TMEM lane quadrant
+constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 8 epilogue warps
 constexpr int kHC = kQT / kEP;            // columns per epilogue thread
 constexpr int kCS = 4;                    // columns per TMEM load step
 constexpr int kNB = 5;                    // tracers per weight group
@@ -71,10 +71,10 @@ constexpr uint32_t kSuspendNs = 1000000;        // longest suspension of one pha
 // (1: order <= 64, 2: order <= 96).
 template <int KC> struct TcCfg {
     static constexpr int LV = KC == 1 ? 5 : 4;              // TMEM accumulator levels
-    static constexpr int kStages = KC == 1 ? 8 : 4;  // 160 KB of basis slices in flight
+    static constexpr int kStages = KC == 1 ? 8 : 4;
     static constexpr uint32_t kStageBytes = KC * kS * kBSliceBytes;
     static constexpr uint32_t kACol = kNBUF * LV * kQT;     // TMEM column of the coefficient slices
-    static constexpr int kYbufFloats = 2 * 4 * (kEP - 1) * kNB * 64;  // [parity][quadrant][part-1][tracer][hi, lo][lane]
+    static constexpr int kYbufFloats = 2 * 4 * kNB * 64;    // [parity][quadrant][tracer][hi, lo][lane]
     static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kCtrlBytes + kEselBytes + kYbufFloats * 4;
 };
 
@@ -443,7 +443,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     int *s_esel = (int *)((unsigned char *)bars + kCtrlBytes);         // selected ells
-    float *ybuf = (float *)((unsigned char *)s_esel + kEselBytes);     // [2][4][kEP-1][NGB][2][32] column-part hand-over
+    float *ybuf = (float *)((unsigned char *)s_esel + kEselBytes);     // [2][4][NGB][2][32] column-half hand-over
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int btile = blockIdx.x % args.nbt;
@@ -715,25 +715,20 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                             Sl[j] = -__fadd_rn(el, __fadd_rn(B2.x, B2.y));
                         }
                     }
-                    // the column parts meet: parts 1.. hand their pairs to part 0 through
+                    // the column halves meet: part 1 hands its pairs to part 0 through
                     // shared memory, double buffered by iteration
-                    float *yq = ybuf + ((size_t)(g & 1) * 4 + quad) * ((kEP - 1) * NGB * 64);
-                    if (part > 0) {
-                        float *slot = yq + (size_t)(part - 1) * NGB * 64;
+                    float *yq = ybuf + ((size_t)(g & 1) * 4 + quad) * (NGB * 64);
+                    if (part == 1) {
 #pragma unroll
-                        for (int j = 0; j < NGB; j++) { slot[j * 64 + lane] = Sh[j]; slot[j * 64 + 32 + lane] = Sl[j]; }
+                        for (int j = 0; j < NGB; j++) { yq[j * 64 + lane] = Sh[j]; yq[j * 64 + 32 + lane] = Sl[j]; }
                     }
                     named_bar_sync(bar_id, 32 * kEP);
                     if (part == 0 && !dead) {
 #pragma unroll
-                        for (int q = 0; q < kEP - 1; q++) {
-                            const float *slot = yq + (size_t)q * NGB * 64;
-#pragma unroll
-                            for (int j = 0; j < NGB; j++) {
-                                float se;
-                                two_sum(Sh[j], slot[j * 64 + lane], Sh[j], se);
-                                Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, slot[j * 64 + 32 + lane]));
-                            }
+                        for (int j = 0; j < NGB; j++) {
+                            float se;
+                            two_sum(Sh[j], yq[j * 64 + lane], Sh[j], se);
+                            Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, yq[j * 64 + 32 + lane]));
                         }
                         if (valid) {
                             // times the tile's scale (exact); the pair (hi, lo) of tracer j at
