@@ -33,14 +33,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "C_l-sets/sec (3x2pt, all bin pairs) mixed vs FP64 at ≤1e-4 rel err; p50/p99 latency"
 UNIT = "C_l-sets/s"
-WORKLOAD = ("3x2pt, 5 clustering + 5 lensing bins (55 spectra), 64 log-spaced ells 2..1000, "
-            "n_chi=128, n_R=128 (R in [0.2,1.8]), Chebyshev order 64, n_kquad=65537")
+WORKLOADS = {
+    "c1": ("3x2pt, 5 clustering + 5 lensing bins (55 spectra), 64 log-spaced ells 2..1000, "
+           "n_chi=128, n_R=128 (R in [0.2,1.8]), Chebyshev order 64, n_kquad=65537"),
+    "c2": ("3x2pt precision grid, 10 clustering + 10 lensing bins (210 spectra), 100 log-spaced ells 2..2000, "
+           "n_chi=256, n_R=192 (R in [0.2,1.8]), Chebyshev order 96, n_kquad=65537"),
+    "c3": ("ragged batch on the 10+10-bin grid: every cosmology with its own bin counts (2..10 of each kind) "
+           "and its own set of 16..100 of the 100 ells, n_chi=256, n_R=192, Chebyshev order 96"),
+}
+WORKLOAD = WORKLOADS["c1"]
 
 
-def workload_config(batch, world):
+def workload_config(batch, world, name="c1"):
     """The workload both arms report (the arithmetic type is the line's dtype)."""
-    return {"workload": WORKLOAD, "batch_per_gpu": batch,
-            "l2": "inputs larger than L2 (basis tables 0.8-1.6 GB per step)",
+    return {"workload": WORKLOADS[name], "batch_per_gpu": batch,
+            "l2": "inputs larger than L2 (basis tables 0.8-14 GB per step)",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
@@ -256,7 +263,8 @@ def run_blast(args):
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    spec = synth.plan_spec("c1")
+    wl = args.workload
+    spec = synth.plan_spec("c1" if wl == "c1" else "c2")
     plan = bl.Plan(spec, device=local)
     cache = args.basis_cache
     if cache and os.path.exists(cache):
@@ -267,12 +275,18 @@ def run_blast(args):
             bl.blast_basis_save(plan.h, cache)
     chi, R, _ = plan.nodes()
     B = args.batch
-    rqs = [synth.config_request("c1", chi, R, i) for i in replica_request_ids(rank, B)]
+    if wl == "c3":
+        made = [synth.ragged_request(chi, R, i, plan.L) for i in replica_request_ids(rank, B)]
+        rqs, sels = [m[0] for m in made], [m[1] for m in made]
+    else:
+        rqs = [synth.config_request(wl, chi, R, i) for i in replica_request_ids(rank, B)]
+        sels = [None] * B
     fields = ["kern_chi", "kern_Rchi", "growth_chi", "growth_Rchi", "k_tab", "p_tab"]
     dev_arrays = [{f: torch.from_numpy(np.ascontiguousarray(getattr(rq, f))).to(dev) for f in fields} for rq in rqs]
-    reqs = [plan.request(rq, device_arrays=d) for rq, d in zip(rqs, dev_arrays)]
-    P = bl.blast_npairs(5, 5)
-    outs = [torch.empty((P, plan.L), dtype=torch.float64, device=dev) for _ in range(B)]
+    reqs = [plan.request(rq, ell_sel=sl, device_arrays=d) for rq, sl, d in zip(rqs, sels, dev_arrays)]
+    P = bl.blast_npairs(spec.max_clust, spec.max_lens)
+    shapes = [(bl.blast_npairs(rq.n_clust, rq.n_lens), plan.L if sl is None else len(sl)) for rq, sl in zip(rqs, sels)]
+    outs = [torch.empty(sh, dtype=torch.float64, device=dev) for sh in shapes]
     out_ptrs = [o.data_ptr() for o in outs]
     stream = torch.cuda.current_stream(dev)
 
@@ -320,7 +334,19 @@ def run_blast(args):
     k64 = max(2, min(20, args.steps // 4))  # FP64 steps: ~150 ms each at the benchmark batch
     ms_64, prof_64 = timed(bl.BLAST_FP64, k64, 1, profile=True)
     C_64 = [o.cpu().numpy() for o in outs]
-    err = max(float(np.max(eij(a, b, 5, 5))) for a, b in zip(C_main, C_64))
+    e_all = [eij(a, b, rq.n_clust, rq.n_lens) for a, b, rq in zip(C_main, C_64, rqs)]
+    err = max(float(np.max(e))for e in e_all)
+    # worst e_ij per (ell, pair type) over the batch (the precision table)
+    from tests.metrics import pair_list
+    table = {}
+    for e, rq, sl in zip(e_all, rqs, sels):
+        types = np.array([t for t, _, _ in pair_list(rq.n_clust, rq.n_lens)])
+        cols = range(plan.L) if sl is None else sl
+        for k, col in enumerate(cols):
+            for t in range(3):
+                if np.any(types == t):
+                    key = (int(spec.ells[col]), t)
+                    table[key] = max(table.get(key, 0.0), float(np.max(e[types == t, k])))
 
     # contraction kernel roofline (dominant kernel of the step)
     kname = "contract_tc" if have_tc else "contract"
@@ -329,7 +355,8 @@ def run_blast(args):
     L, N, Q, X = plan.L, plan.N, plan.Q, plan.X
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    method_flops = 2.0 * 3 * L * N * Q * B          # contraction (a), one multiply-add per product
+    # contraction (a), one multiply-add per product, over each cosmology's own ells
+    method_flops = sum(2.0 * 3 * (L if sl is None else len(sl)) * N * Q for sl in sels)
     if have_tc:
         # the roofline flops: the method's products with the split-MMA allowance x3;
         # the kernel is timed alone in its launch, so the burst BF16 peak applies
@@ -365,7 +392,8 @@ def run_blast(args):
         Bp = -(-B // 128) * 128
         # R-tile partial pairs of every padded cosmology, chi weights (hi, lo) of the
         # A-side kind per type, and the C_l written
-        red_bytes = Bp * 3 * L * X * (plan.Rn // 32) * MT * 8 + 3 * Bp * X * MT * 8 + B * P * L * 8
+        red_bytes = (Bp * 3 * L * X * (plan.Rn // 32) * MT * 8 + 3 * Bp * X * MT * 8
+                     + sum(sh[0] * sh[1] for sh in shapes) * 8)
         gbs = red_bytes / (rms / rl * 1e-3) / 1e9
         kern["reduce"] = {"bound": "hbm", "bytes_per_launch": red_bytes, "achieved": gbs,
                           "peak": peaks.get("hbm_gbs"), "frac": gbs / peaks.get("hbm_gbs", 6800.0),
@@ -405,13 +433,13 @@ def run_blast(args):
             d[f] = t
             h2d += arr.nbytes
         host.append(d)
-    hreqs = [plan.request(rq, device_arrays=None) for rq in rqs]
+    hreqs = [plan.request(rq, ell_sel=sl, device_arrays=None) for rq, sl in zip(rqs, sels)]
     for hr, d in zip(hreqs, host):  # point the host request at pinned copies
         hr.kern_chi, hr.kern_Rchi = d["kern_chi"].data_ptr(), d["kern_Rchi"].data_ptr()
         hr.growth_chi, hr.growth_Rchi = d["growth_chi"].data_ptr(), d["growth_Rchi"].data_ptr()
         hr.k_tab, hr.p_tab = d["k_tab"].data_ptr(), d["p_tab"].data_ptr()
         hr._keep = d
-    houts = [torch.empty((P, plan.L), dtype=torch.float64, pin_memory=True) for _ in range(B)]
+    houts = [torch.empty(sh, dtype=torch.float64, pin_memory=True) for sh in shapes]
     hptrs = [o.data_ptr() for o in houts]
     d2h = sum(o.numel() * 8 for o in houts)
 
@@ -430,7 +458,7 @@ def run_blast(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
 
     serve = None
-    if args.serve_seconds > 0 and rank == 0:
+    if args.serve_seconds > 0 and rank == 0 and wl == "c1":
         serve = serve_latency(plan, rqs, prec_main, dtype_main, args.serve_rate, args.serve_seconds)
 
     launches = sum(prof_main[n][1] for n in bl.KERNEL_CLASS_NAMES)
@@ -439,11 +467,13 @@ def run_blast(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_main / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_main, "data": "synthetic",
-        "config": workload_config(B, world),
+        "config": workload_config(B, world, wl),
         "fp64": {"value": job_throughput(world, B, k64, ms_64 * 1e-3), "unit": UNIT, "ms_per_step": ms_64 / k64,
                  "dtype": "f64"},
         "err_vs_fp64": {"max_eij": err, "bound": 1e-4,
-                        "def": "|C-C_fp64|/sqrt(C_ii C_jj), every cosmology of the batch, all pairs and ells"},
+                        "def": "|C-C_fp64|/sqrt(C_ii C_jj), every cosmology of the batch, all pairs and ells",
+                        "by_ell_type": {f"{l}:{'gg gs ss'.split()[t]}": v for (l, t), v in sorted(table.items())}
+                        if wl != "c1" else None},
         "latency_ms": serve,
         "sequential_fp64_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                "req_per_s": 1e3 * len(lat) / sum(lat),
@@ -458,7 +488,7 @@ def run_blast(args):
                                 if prof_main[n][1]},
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl == "c1":
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -533,6 +563,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--impl", default="blast", choices=["blast", "reference"])
+    ap.add_argument("--workload", default="c1", choices=sorted(WORKLOADS),
+                    help="c1: the 3x2pt 5+5-bin grid (default); c2: the 10+10-bin order-96 grid; "
+                         "c3: ragged bins and ell sets on the c2 grid")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=2000.0,
                     help="offered request rate of the serving-latency run (requests/s)")

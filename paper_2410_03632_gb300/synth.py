@@ -249,6 +249,20 @@ def plan_spec(name: str) -> PlanSpec:
                     kquad_points(1e-4, 10.0, cmax, 1.8), ng, ns)
 
 
+def ragged_request(chi, R, idx: int, n_ell: int):
+    """Request idx of the ragged batch on the 10+10-bin grid: its own tracer
+    counts drawn from 2..10 of each kind, its own ell set (a random subset of
+    16..n_ell of the plan's ells) and cosmology (seed 1003 + 7919 idx).
+    Returns (Request, sorted list of selected plan-ell indices)."""
+    rng = np.random.default_rng(1003 + 7919 * idx)
+    ng, ns = int(rng.integers(2, 11)), int(rng.integers(2, 11))
+    k = int(rng.integers(16, n_ell + 1))
+    sel = sorted(int(x) for x in rng.choice(n_ell, size=k, replace=False))
+    n2, a_w = rng.uniform(-2.5, -1.5), rng.uniform(0.03, 0.08)
+    phi, Om, s8 = rng.uniform(0.0, 2 * np.pi), rng.uniform(0.25, 0.35), rng.uniform(0.7, 0.9)
+    return make_request(chi, R, ng, ns, Om=Om, n2=n2, a_w=a_w, phi=phi, s8=s8), sel
+
+
 def config_request(name: str, chi, R, idx: int = 0) -> Request:
     """The seeded request of a workload: seed 1000 + config + 7919 idx."""
     spec = plan_spec(name)
