@@ -54,15 +54,16 @@ constexpr int kS = BLAST_TC_SLICES;       // slices per operand
 constexpr int kQT = 32;                   // chi-R nodes per tile (MMA N)
 constexpr int kM = 128;                   // cosmologies per tile (MMA M)
 constexpr int kKC = 64;                   // K elements per 128-byte swizzle row (one TMA box)
-constexpr int kEP = 2;                    // epilogue warps per TMEM lane quadrant (one per buffer)
+constexpr int kEP = 2;                    // epilogue warps per TMEM lane quadrant
 constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 8 epilogue warps
-constexpr int kCS = 16;                   // columns per TMEM load step (two steps per tile)
+constexpr int kHC = kQT / kEP;            // columns per epilogue thread
+constexpr int kCS = 4;                    // columns per TMEM load step
 constexpr int kNB = 5;                    // tracers per weight group
 constexpr int kNBUF = 2;                  // TMEM accumulator buffers
 constexpr uint32_t kBSliceBytes = kQT * 128;  // 32 rows x 64 bf16
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kCtrlBytes = 256;          // mbarriers, TMEM address, abort flag
-constexpr uint32_t kEselBytes = 4 * BLAST_MAX_ELL;
+constexpr uint32_t kEselBytes = 4 * BLAST_MAX_ELL;  // selected ells
 constexpr long long kWaitLimit = 4000000000LL;  // clock cycles (about 2 s)
 constexpr uint32_t kSuspendNs = 1000000;        // longest suspension of one phase test
 
@@ -70,12 +71,11 @@ constexpr uint32_t kSuspendNs = 1000000;        // longest suspension of one pha
 // (1: order <= 64, 2: order <= 96).
 template <int KC> struct TcCfg {
     static constexpr int LV = KC == 1 ? 5 : 4;              // TMEM accumulator levels
-    static constexpr int kStages = KC == 1 ? 7 : 3;
+    static constexpr int kStages = KC == 1 ? 8 : 4;
     static constexpr uint32_t kStageBytes = KC * kS * kBSliceBytes;
     static constexpr uint32_t kACol = kNBUF * LV * kQT;     // TMEM column of the coefficient slices
-    // quadrature weights of one tracer group: [tracer][column pair][cosmology of the tile] FP32 pairs
-    static constexpr size_t kVsmBytes = (size_t)kNB * (kQT / 2) * kM * 8;
-    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kCtrlBytes + kEselBytes + kVsmBytes;
+    static constexpr int kYbufFloats = 2 * 4 * kNB * 64;    // [parity][quadrant][tracer][hi, lo][lane]
+    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kCtrlBytes + kEselBytes + kYbufFloats * 4;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -192,35 +192,23 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                 "%14, %15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                  : "r"(taddr));
 }
 
-// Wait for this thread's TMEM loads; the registers they fill are operands, so
-// no use of them can move above the wait.
-__device__ __forceinline__ void tmem_wait_ld16(uint32_t (&r)[16])
+__device__ __forceinline__ void tmem_wait_ld4(uint32_t (&r)[4])
 {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
-                 :
-                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
 }
 
 // Register fence for values a tcgen05.wait::ld has already covered: ties
 // them to a point after that wait.
-__device__ __forceinline__ void reg_fence16(uint32_t (&r)[16])
+__device__ __forceinline__ void reg_fence4(uint32_t (&r)[4])
 {
-    asm volatile(""
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
-                 :
-                 : "memory");
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]) : : "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -427,9 +415,10 @@ struct TcArgs {
     int *err;            // host-mapped error word
 };
 
-// Work units: (cosmology tile, tracer group, 32-column q tile); a CTA keeps
-// its cosmology tile (grid a multiple of nbt), so the coefficient slices stay
-// in TMEM for the whole launch.  Each unit runs the 3 n_esel (type, ell) tiles.
+// Work units: (cosmology tile, group of five B-side tracers, 32-column q
+// tile).  A CTA keeps its cosmology tile (the grid is a multiple of nbt), so
+// the coefficient slices stay in TMEM for the whole launch; each unit runs
+// the 3 n_esel (type, ell) tiles of its q tile.
 __device__ __forceinline__ void unit_decode(const TcArgs &a, int u, int &grp, int &q0)
 {
     grp = (u / a.nbt) % a.ngr;
@@ -443,17 +432,18 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     using C = TcCfg<KC>;
     constexpr int LV = C::LV;
     constexpr int kStages = C::kStages;
+    constexpr int NGB = kNB;  // B-side tracers of one unit
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzled tiles
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sB = smem;                                              // kStages x KC x kS x 4 KB
+    unsigned char *sB = smem;                                         // kStages x KC x kS x 4 KB
     uint64_t *bars = (uint64_t *)(sB + (size_t)kStages * C::kStageBytes);  // kCtrlBytes of control words
     uint64_t *full = bars, *empty = bars + kStages, *aready = bars + 2 * kStages;
     uint64_t *tfull = aready + 1, *tempty = tfull + kNBUF, *mdone = tempty + kNBUF;
     uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    int *s_esel = (int *)((unsigned char *)bars + kCtrlBytes);           // selected ells
-    f32x2 *vsm = (f32x2 *)((unsigned char *)s_esel + kEselBytes);         // [kNB][16][kM] weights
+    int *s_esel = (int *)((unsigned char *)bars + kCtrlBytes);         // selected ells
+    float *ybuf = (float *)((unsigned char *)s_esel + kEselBytes);     // [2][4][NGB][2][32] column-half hand-over
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int btile = blockIdx.x % args.nbt;
@@ -463,7 +453,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; i++) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         mbar_init(aready, 128);
-        for (int i = 0; i < kNBUF; i++) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128); }
+        for (int i = 0; i < kNBUF; i++) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128 * kEP); }
         mbar_init(mdone, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -575,13 +565,11 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         mbar_wait(mdone, 0, 64);
         __syncwarp();
     } else {
-        // ------------------------------------------------ epilogue: two warps per TMEM lane quadrant,
-        // one per accumulator buffer: the warp of parity `part` takes the tiles
-        // g = part (mod 2), all 32 columns, so the quadrant's two warps work a tile
-        // apart.  A thread owns one cosmology (TMEM lane).
+        // ------------------------------------------------ epilogue: kEP warps per TMEM lane quadrant;
+        // a thread owns one cosmology (TMEM lane) and kHC of the tile's 32 columns.
         const int ew = warp - 2;
-        const int quad = warp & 3;  // lanes 32 quad .. 32 quad + 31 are readable by this warp
-        const int part = ew >> 2;   // tile parity = accumulator buffer
+        const int quad = warp & 3;   // lanes 32 quad .. 32 quad + 31 are readable by this warp
+        const int part = ew >> 2;    // columns [kHC part, kHC part + kHC)
         const int bl_ = quad * 32 + lane;
         const int b = btile * kM + bl_;
         const bool valid = b < args.n;
@@ -589,6 +577,8 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         const int ng = valid ? rq->n_clust : 0, ns = valid ? rq->n_lens : 0;
         const float sa = args.sa[b];
         const uint32_t lane_addr = ((uint32_t)(quad * 32)) << 16;
+        const int cb = part * kHC;
+        const int tid_e = threadIdx.x - 64;  // 0 .. 128 kEP - 1
         if (part == 0) {
             // coefficient slices of cosmology b -> TMEM lane b, columns kACol + (Kmma/2) p ..
             const int acol = args.Kmma / 2;
@@ -606,12 +596,13 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
             tc_fence_before();
             mbar_arrive(aready);
         }
-        // The quadrant's two warps meet at a named barrier only when the
-        // weights change (start of the gg and gs phases of a unit); both pass
-        // it the same number of times whatever happens to their waits.
+        // Every thread of the quadrant's two warps passes the same number of
+        // named barriers; after a wait runs out the warps skip the work but keep
+        // the count, so no barrier is left waiting.
         const int bar_id = 1 + quad;
         uint32_t g = 0;
         bool dead = false;
+        f32x2 vr[kNB][kHC / 2];  // quadrature weights (times 2^ea) of tracers 0..4 of the B-side kind
         for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
             int grp, q0;
             unit_decode(args, u, grp, q0);
@@ -619,32 +610,29 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
             for (int t = 0; t < 3; t++) {
                 const int offB = (t == 0) ? 0 : ng, nB = (t == 0) ? ng : ns;
                 if (t < 2) {
-                    // weights of the B-side kind (clustering for gg, lensing for gs and ss),
-                    // tracers kNB grp .. kNB grp + 4, times 2^ea: this thread's 8 column
-                    // pairs [8 part, 8 part + 8) for its cosmology
-                    named_bar_sync(bar_id, 64);  // the other warp is done with the old weights
+                    // weights of the B-side kind (clustering for gg, lensing for gs and
+                    // ss), tracers 5 grp .. 5 grp + 4 of it
 #pragma unroll
                     for (int j = 0; j < kNB; j++) {
                         const int jj = kNB * grp + j;
                         const float4 *src =
                             (valid && jj < nB)
-                                ? reinterpret_cast<const float4 *>(rq->V32 + (size_t)(offB + jj) * args.Q + q0 + 16 * part)
+                                ? reinterpret_cast<const float4 *>(rq->V32 + (size_t)(offB + jj) * args.Q + q0 + cb)
                                 : nullptr;
 #pragma unroll
-                        for (int c = 0; c < 4; c++) {
+                        for (int c = 0; c < kHC / 4; c++) {
                             const float4 v = src ? src[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-                            vsm[(j * 16 + 8 * part + 2 * c) * kM + bl_] = pk2(v.x * sa, v.y * sa);
-                            vsm[(j * 16 + 8 * part + 2 * c + 1) * kM + bl_] = pk2(v.z * sa, v.w * sa);
+                            vr[j][2 * c] = pk2(v.x * sa, v.y * sa);
+                            vr[j][2 * c + 1] = pk2(v.z * sa, v.w * sa);
                         }
                     }
-                    named_bar_sync(bar_id, 64);  // weights ready
                 }
                 for (int es = 0; es < args.n_esel; es++, g++) {
-                    if ((int)(g & 1) != part) continue;  // the other warp's tile
-                    const int buf = part;
-                    const uint32_t tph = (g >> 1) & 1;
+                    const int buf = g % kNBUF;
+                    const uint32_t tph = (g / kNBUF) & 1;
                     // the tile's scale 2^(eG - 16), fetched while the MMA finishes
-                    const float tsc = args.scT[((size_t)t * args.L + s_esel[es]) * (args.Q / kQT) + q0 / kQT];
+                    const float tsc =
+                        (part == 0) ? args.scT[((size_t)t * args.L + s_esel[es]) * (args.Q / kQT) + q0 / kQT] : 0.f;
                     if (!dead) {
                         bool lost = *abort_flag != 0;
                         if (!lost && !mbar_wait(&tfull[buf], tph)) {
@@ -654,82 +642,105 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                         }
                         dead = __any_sync(0xffffffffu, lost);
                     }
-                    if (dead) continue;
-                    tc_fence_after();
-                    const uint32_t tcol = tmem + lane_addr + buf * (LV * kQT);
-                    // R-sum of the tile's 32 columns, two columns per packed lane pair, as
-                    // negated unevaluated sums An + Bn: each product V w is split exactly
-                    // (FMA), the two products of a lane pair are added plainly, and each
-                    // addition of those sums keeps its rounding error (two-sum), so the
-                    // sum survives the cancellation of oscillating w
-                    f32x2 An[kNB], Bn[kNB];
+                    float Sh[NGB], Sl[NGB];
 #pragma unroll
-                    for (int half = 0; half < kQT / kCS; half++) {
-                        uint32_t D[LV][kCS];
+                    for (int j = 0; j < NGB; j++) { Sh[j] = 0.f; Sl[j] = 0.f; }
+                    if (!dead) {
+                        tc_fence_after();
+                        const uint32_t tcol = tmem + lane_addr + buf * (LV * kQT) + cb;
+                        // R-sum of this thread's columns, two columns per packed lane pair, as
+                        // negated unevaluated sums An + Bn: each product V w is split exactly
+                        // (FMA), the two products of a lane pair are added plainly, and each
+                        // addition of those sums keeps its rounding error (two-sum), so the
+                        // sum survives the cancellation of oscillating w
+                        f32x2 An[NGB], Bn[NGB];
 #pragma unroll
-                        for (int lev = 0; lev < LV; lev++) tmem_ld16(tcol + lev * kQT + half * kCS, D[lev]);
-                        tmem_wait_ld16(D[0]);
+                        for (int s = 0; s < kHC / kCS; s++) {
+                            uint32_t D[LV][kCS];
 #pragma unroll
-                        for (int lev = 1; lev < LV; lev++) reg_fence16(D[lev]);
-                        if (half + 1 == kQT / kCS) {  // every level of this buffer is in registers: release it
-                            tc_fence_before();
-                            mbar_arrive(&tempty[buf]);
-                        }
+                            for (int lev = 0; lev < LV; lev++) tmem_ld4(tcol + lev * kQT + s * kCS, D[lev]);
+                            tmem_wait_ld4(D[0]);
 #pragma unroll
-                        for (int ch = 0; ch < kCS / 4; ch++) {
+                            for (int lev = 1; lev < LV; lev++) reg_fence4(D[lev]);
+                            if (s + 1 == kHC / kCS) {  // every level of this buffer is in registers: release it
+                                tc_fence_before();
+                                mbar_arrive(&tempty[buf]);
+                            }
                             // levels 0..2 are exact multiples of their quanta, so both fast
                             // two-sums are exact; the small parts add plainly (one rounding)
-                            f32x2 m[2], lo[2];
+                            f32x2 m[kCS / 2], lo[kCS / 2];
 #pragma unroll
-                            for (int h = 0; h < 2; h++) {
-                                const int c = 4 * ch + 2 * h;
+                            for (int h = 0; h < kCS / 2; h++) {
                                 f32x2 d[LV];
 #pragma unroll
                                 for (int lev = 0; lev < LV; lev++)
-                                    d[lev] = pk2(__uint_as_float(D[lev][c]), __uint_as_float(D[lev][c + 1]));
+                                    d[lev] = pk2(__uint_as_float(D[lev][2 * h]), __uint_as_float(D[lev][2 * h + 1]));
                                 f32x2 e1, e2;
                                 fast_two_sum2(d[0], d[1], m[h], e1);
                                 fast_two_sum2(m[h], d[2], m[h], e2);
                                 const f32x2 small = (LV == 5) ? add2(d[3], d[LV - 1]) : d[3];
                                 lo[h] = add2(add2(e1, e2), small);
                             }
-                            const f32x2 mn0 = neg2(m[0]), mn1 = neg2(m[1]);
-                            const int pc = half * (kCS / 2) + 2 * ch;  // packed column pair of lane pair 0
-                            const bool first = (half == 0 && ch == 0);
 #pragma unroll
-                            for (int j = 0; j < kNB; j++) {
-                                const f32x2 v0 = vsm[(j * 16 + pc) * kM + bl_], v1 = vsm[(j * 16 + pc + 1) * kM + bl_];
-                                const f32x2 p0 = mul2(v0, mn0), p1 = mul2(v1, mn1);      // -fl(v m)
-                                const f32x2 e0 = fma2(v0, lo[0], fma2(v0, m[0], p0));    // v lo + (v m - fl(v m))
-                                const f32x2 e1 = fma2(v1, lo[1], fma2(v1, m[1], p1));
-                                const f32x2 ps = add2(p0, p1), pe = add2(e0, e1);
-                                if (first) {  // the sums start here
-                                    An[j] = ps;
-                                    Bn[j] = neg2(pe);
-                                } else {
-                                    f32x2 se;
-                                    two_sum2(An[j], ps, An[j], se);
-                                    Bn[j] = add2(Bn[j], sub2(se, pe));
+                            for (int ch = 0; ch < kCS / 4; ch++) {
+                                const int h0 = 2 * ch, h1 = 2 * ch + 1;
+                                const f32x2 mn0 = neg2(m[h0]), mn1 = neg2(m[h1]);
+                                const bool first = (s == 0 && ch == 0);
+#pragma unroll
+                                for (int j = 0; j < NGB; j++) {
+                                    const int pc = s * (kCS / 2) + h0;  // packed column pair index
+                                    const f32x2 v0 = vr[j][pc], v1 = vr[j][pc + 1];
+                                    const f32x2 p0 = mul2(v0, mn0), p1 = mul2(v1, mn1);   // -fl(v m)
+                                    const f32x2 e0 = fma2(v0, lo[h0], fma2(v0, m[h0], p0));  // v lo + (v m - fl(v m))
+                                    const f32x2 e1 = fma2(v1, lo[h1], fma2(v1, m[h1], p1));
+                                    const f32x2 ps = add2(p0, p1), pe = add2(e0, e1);
+                                    if (first) {  // the sums start here
+                                        An[j] = ps;
+                                        Bn[j] = neg2(pe);
+                                    } else {
+                                        f32x2 se;
+                                        two_sum2(An[j], ps, An[j], se);
+                                        Bn[j] = add2(Bn[j], sub2(se, pe));
+                                    }
                                 }
                             }
                         }
-                    }
-                    if (valid) {
-                        // both lanes into one pair per tracer, S = -(An.x + An.y) - (Bn.x + Bn.y),
-                        // times the tile scale (exact); the pair (hi, lo) of tracer j at
-                        // Y[t][es][a][b / 32][rt][j][hi, lo][b % 32]: a warp stores 128 bytes
-                        float *y = args.Y +
-                                   (((((size_t)t * args.n_esel + es) * args.X + a) * (args.Bpad / 32) + (b >> 5)) *
-                                        args.RT + rt) * (size_t)args.MT * 64 + lane;
+                        // both lanes into one pair per tracer: S = -(An.x + An.y) - (Bn.x + Bn.y)
 #pragma unroll
-                        for (int j = 0; j < kNB; j++) {
-                            const int jj = kNB * grp + j;
-                            if (jj >= args.MT) break;
+                        for (int j = 0; j < NGB; j++) {
                             const float2 A2 = unpk2(An[j]), B2 = unpk2(Bn[j]);
                             float h, el;
                             two_sum(A2.x, A2.y, h, el);
-                            y[jj * 64] = -h * tsc;
-                            y[jj * 64 + 32] = -__fadd_rn(el, __fadd_rn(B2.x, B2.y)) * tsc;
+                            Sh[j] = -h;
+                            Sl[j] = -__fadd_rn(el, __fadd_rn(B2.x, B2.y));
+                        }
+                    }
+                    // the column halves meet: part 1 hands its pairs to part 0 through
+                    // shared memory, double buffered by iteration
+                    float *yq = ybuf + ((size_t)(g & 1) * 4 + quad) * (NGB * 64);
+                    if (part == 1) {
+#pragma unroll
+                        for (int j = 0; j < NGB; j++) { yq[j * 64 + lane] = Sh[j]; yq[j * 64 + 32 + lane] = Sl[j]; }
+                    }
+                    named_bar_sync(bar_id, 32 * kEP);
+                    if (part == 0 && !dead) {
+#pragma unroll
+                        for (int j = 0; j < NGB; j++) {
+                            float se;
+                            two_sum(Sh[j], yq[j * 64 + lane], Sh[j], se);
+                            Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, yq[j * 64 + 32 + lane]));
+                        }
+                        if (valid) {
+                            // times the tile's scale (exact); the pair (hi, lo) of tracer j at
+                            // Y[t][es][a][b / 32][rt][j][hi, lo][b % 32]: a warp stores 128 bytes
+                            float *y = args.Y +
+                                       (((((size_t)t * args.n_esel + es) * args.X + a) * (args.Bpad / 32) + (b >> 5)) *
+                                            args.RT + rt) * (size_t)args.MT * 64 + lane;
+#pragma unroll
+                            for (int j = 0; j < NGB; j++) {
+                                const int jj = kNB * grp + j;
+                                if (jj < args.MT) { y[jj * 64] = Sh[j] * tsc; y[jj * 64 + 32] = Sl[j] * tsc; }
+                            }
                         }
                     }
                 }
@@ -815,6 +826,7 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
             sh[j] = 0.f;
             sl[j] = 0.f;
             if (j < nB) {
+#pragma unroll 2
                 for (int rt = 0; rt < RT; rt++) {
                     const float yh = v[(rt * MT + j) * 64 + lane], yl = v[(rt * MT + j) * 64 + 32 + lane];
                     float se;
@@ -1028,11 +1040,11 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
         reinterpret_cast<const float *>(p->ws.tc.as<char>() + tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad));
     const int RT = p->Rn / kQT, MT = p->max_tr;
     const size_t stage = ((size_t)RT * MT * 64 + 2 * MT * 32) * 4;
-    // 4 warps (chi chunks), 2 for large stages, with as many stages each as fit
+    // 8 warps (chi chunks), 2 for large stages, with as many stages each as fit
     // two blocks per SM
-    const int W = stage > 8192 ? 2 : 4;
+    const int W = stage > 8192 ? 2 : 8;
     int NS = (int)((110 * 1024) / (W * (stage + 8)));
-    if (NS > 6) NS = 6;
+    if (NS > 4) NS = 4;
     if (NS < 1) return BLAST_EINVAL;
     const size_t smem = (size_t)W * NS * (stage + 8);
     const bool big = MT > kNB;
