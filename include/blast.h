@@ -190,6 +190,21 @@ int blast_cl(blast_plan *plan, const blast_request *req, int precision,
 int blast_cl_batch(blast_plan *plan, int n, const blast_request *reqs, int precision,
                    double *const *outs, int out_mem_space, void *stream);
 
+/* Coefficient envelope of BLAST_BF16S.  The five slices hold each cosmology's
+ * Chebyshev coefficients to 40 bits of its largest one; since the coefficients
+ * of a power spectrum fall by decades with n, basis row n is scaled by a power
+ * of two s_n and the coefficients by 1 / s_n (exact, the products unchanged),
+ * so every term a_n T~_n keeps its 40 bits.  env[n_cheb] > 0 gives the shape
+ * (rounded to powers of two, at most 2^16 below its maximum); NULL restores
+ * the default, the running maximum of the coefficients of a generic linear
+ * power spectrum x / (1 + x^3), x = k / 0.02 h/Mpc, held at or above 2^-8 of
+ * its first value (tabulated spectra keep high-n coefficients of that
+ * order; an envelope below a cosmology's own coefficients costs precision
+ * instead of gaining it).  The slice tables are
+ * rebuilt if present.  Errors: BLAST_EINVAL (a non-positive entry),
+ * BLAST_EDEVICE. */
+int blast_set_coef_envelope(blast_plan *plan, const double *env);
+
 /* Allocation-free evaluation.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory while evaluating,
  * for example a host framework that has reserved the GPU's memory for its own

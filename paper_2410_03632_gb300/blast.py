@@ -83,6 +83,7 @@ def lib():
             L.blast_status_str.argtypes = [i]
             L.blast_status_str.restype = ctypes.c_char_p
             L.blast_cl_noalloc.argtypes = [P, ctypes.POINTER(blast_request), P, P]
+            L.blast_set_coef_envelope.argtypes = [P, P]
             L.blast_profile_enable.argtypes = [P, i]
             L.blast_profile_read.argtypes = [P, i, _dp, ctypes.POINTER(ctypes.c_longlong)]
             L.blast_profile_reset.argtypes = [P]
@@ -141,6 +142,14 @@ def blast_cl_noalloc(h, req, out_ptr, stream=None):
     """FP64 C_l of one cosmology without any device allocation (device inputs
     and output); scratch comes from a fixed array inside the library."""
     return lib().blast_cl_noalloc(h, ctypes.byref(req), out_ptr, stream)
+
+
+def blast_set_coef_envelope(h, env=None):
+    """env: numpy float64 array of n_cheb positive values, or None for the default."""
+    if env is None:
+        return lib().blast_set_coef_envelope(h, None)
+    env = np.ascontiguousarray(env, dtype=np.float64)
+    return lib().blast_set_coef_envelope(h, env.ctypes.data)
 
 
 def blast_request_footprint(h, req):

@@ -63,6 +63,8 @@ struct blast_plan {
     double *d_kcheb_u = nullptr;   // ln k of each Chebyshev node
     double *d_cos_tab = nullptr;   // cos(pi p / 2N), p < 4N
     double *d_pref = nullptr;      // N_AB(l) [3][L]
+    std::vector<double> env;       // power-of-two coefficient envelope s_n of the tensor-core path
+    double *d_env = nullptr;
 
     // basis tables
     double *T64 = nullptr;          // [3][L][N][Q]
@@ -135,6 +137,7 @@ size_t tc_y_bytes(const blast_plan *p, int n, int n_esel);  // R-tile partials o
 
 // Host helpers
 int plan_alloc_basis(blast_plan *p, unsigned mask);
+void default_envelope(const blast_plan *p, std::vector<double> &env);  // generic linear-P coefficient envelope
 int request_check(const blast_plan *p, const blast_request *r);  // the checks of blast_cl
 int request_n_sel(const blast_plan *p, const blast_request *r);  // ells selected by the mask
 double host_now();

@@ -69,13 +69,19 @@ constexpr uint32_t kSuspendNs = 1000000;        // longest suspension of one pha
 
 // Compile-time shape of one kernel instance: KC 64-wide K chunks per stage
 // (1: order <= 64, 2: order <= 96).
+// Both keep five exact TMEM levels; with two K chunks the coefficient slices
+// 0..3 fill the TMEM left beside the accumulators and slice 4 (one slice pair,
+// p = 4, q = 0, per K step) is read from shared memory.
 template <int KC> struct TcCfg {
-    static constexpr int LV = KC == 1 ? 5 : 4;              // TMEM accumulator levels
+    static constexpr int LV = 5;                            // TMEM accumulator levels
     static constexpr int kStages = KC == 1 ? 8 : 4;
     static constexpr uint32_t kStageBytes = KC * kS * kBSliceBytes;
     static constexpr uint32_t kACol = kNBUF * LV * kQT;     // TMEM column of the coefficient slices
+    static constexpr int kSliceTmem = KC == 1 ? kS : kS - 1;  // coefficient slices held in TMEM
+    static constexpr uint32_t kA4Bytes = KC == 1 ? 0 : KC * kM * 128;  // slice 4: [chunk][128 rows][128 B]
     static constexpr int kYbufFloats = 2 * 4 * kNB * 64;    // [parity][quadrant][tracer][hi, lo][lane]
-    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kCtrlBytes + kEselBytes + kYbufFloats * 4;
+    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kA4Bytes + kCtrlBytes + kEselBytes +
+                                    kYbufFloats * 4;
 };
 
 // ---------------------------------------------------------------- PTX helpers
@@ -148,6 +154,14 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row groups 1024 bytes apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
@@ -174,6 +188,16 @@ __device__ __forceinline__ void umma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
         ::"r"(d_tmem), "r"(a_tmem), "l"(bd), "r"(kIdesc), "r"(acc));
+}
+
+// MMA with both operands in shared memory (A: kM rows x 16 BF16, K-major).
+__device__ __forceinline__ void umma_ss(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
 }
 
 // True in exactly one lane of the (converged) warp.
@@ -335,19 +359,20 @@ __device__ __forceinline__ void slice8(double xn, uint16_t (&out)[kS], float f =
 //   U[bt][a][kind][hl][i][lane],  b = 32 bt + lane,  i < MT (zero past the
 //   request's tracer count), kind 0 clustering, 1 lensing.
 __global__ void k_coef_slices(const ReqDev *__restrict__ reqs, int n, int N, int Kst, int Bpad, uint16_t *A,
-                              float *sa, int X, int MT, float *U)
+                              float *sa, int X, int MT, float *U, const double *__restrict__ env)
 {
     const int b = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
     if (b >= Bpad) return;
     const double *a = (b < n) ? reqs[b].a64 : nullptr;
+    // a_n / s_n: the basis rows carry s_n (powers of two, so both scalings are exact)
     double mx = 0.0;
-    for (int k = lane; k < N; k += 32) mx = fmax(mx, fabs(a ? a[k] : 0.0));
+    for (int k = lane; k < N; k += 32) mx = fmax(mx, fabs(a ? a[k] / env[k] : 0.0));
     for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     int e = 0;
     if (mx > 0.0) frexp(mx, &e);  // mx = f 2^e, f in [0.5, 1)
     for (int k = lane; k < Kst; k += 32) {
         uint16_t s[kS];
-        slice8((a && k < N) ? ldexp(a[k], -e) : 0.0, s);
+        slice8((a && k < N) ? ldexp(a[k] / env[k], -e) : 0.0, s);
 #pragma unroll
         for (int p = 0; p < kS; p++) A[((size_t)p * Bpad + b) * Kst + k] = s[p];
     }
@@ -374,7 +399,7 @@ __global__ void k_coef_slices(const ReqDev *__restrict__ reqs, int n, int N, int
 // largest (or in tiles whose scale underflows FP32) are zero: they could not
 // change the tile's sum.
 __global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q, int Kst, uint16_t *Tsl,
-                               float *scT)
+                               float *scT, const double *__restrict__ env)
 {
     const size_t ncol = (size_t)3 * L * Q;
     const size_t ntile = ncol / kQT;
@@ -385,7 +410,7 @@ __global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q
         const size_t tl = col / Q, q = col % Q;
         const double *src = T + tl * (size_t)N * Q + q;
         double mx = 0.0;
-        for (int k = 0; k < N; k++) mx = fmax(mx, fabs(src[(size_t)k * Q]));
+        for (int k = 0; k < N; k++) mx = fmax(mx, fabs(src[(size_t)k * Q] * env[k]));
         int e = 0;
         if (mx > 0.0) frexp(mx, &e);
         int eG = (mx > 0.0) ? e : INT_MIN;
@@ -395,7 +420,7 @@ __global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q
         const float shift = keep ? ldexpf(1.0f, e - eG) : 0.0f;
         for (int k = 0; k < Kst; k++) {
             uint16_t s[kS];
-            slice8((k < N && keep) ? ldexp(src[(size_t)k * Q], -e) : 0.0, s, shift);
+            slice8((k < N && keep) ? ldexp(src[(size_t)k * Q] * env[k], -e) : 0.0, s, shift);
 #pragma unroll
             for (int p = 0; p < kS; p++) Tsl[((size_t)p * ncol + col) * Kst + k] = s[p];
         }
@@ -411,7 +436,7 @@ struct TcArgs {
     const float *scT;    // [3][L][Q / kQT] one scale per tile
     const float *sa;     // [Bpad]
     const uint16_t *A;   // [S][Bpad][Kst] coefficient slices
-    float *Y;            // [3][n_esel][X][Bpad/32][RT][MT][hi, lo][32] R-tile partial pairs
+    float *Y;            // [3][n_esel][X][Bpad/32][ngr][RT][5][hi, lo][32] R-tile partial pairs
     int *err;            // host-mapped error word
 };
 
@@ -427,7 +452,7 @@ __device__ __forceinline__ void unit_decode(const TcArgs &a, int u, int &grp, in
 
 template <int KC>
 __global__ void __launch_bounds__(kThreads, 1)
-k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
+k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ CUtensorMap mapA4, TcArgs args)
 {
     using C = TcCfg<KC>;
     constexpr int LV = C::LV;
@@ -437,10 +462,11 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
     // 1024-byte alignment for the swizzled tiles
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sB = smem;                                         // kStages x KC x kS x 4 KB
-    uint64_t *bars = (uint64_t *)(sB + (size_t)kStages * C::kStageBytes);  // kCtrlBytes of control words
+    unsigned char *sA4 = sB + (size_t)kStages * C::kStageBytes;        // coefficient slice 4 (order > 64)
+    uint64_t *bars = (uint64_t *)(sA4 + C::kA4Bytes);                   // kCtrlBytes of control words
     uint64_t *full = bars, *empty = bars + kStages, *aready = bars + 2 * kStages;
-    uint64_t *tfull = aready + 1, *tempty = tfull + kNBUF, *mdone = tempty + kNBUF;
-    uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
+    uint64_t *tfull = aready + 1, *tempty = tfull + kNBUF, *mdone = tempty + kNBUF, *a4ready = mdone + 1;
+    uint32_t *tmem_slot = (uint32_t *)(a4ready + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     int *s_esel = (int *)((unsigned char *)bars + kCtrlBytes);         // selected ells
     float *ybuf = (float *)((unsigned char *)s_esel + kEselBytes);     // [2][4][NGB][2][32] column-half hand-over
@@ -455,6 +481,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         mbar_init(aready, 128);
         for (int i = 0; i < kNBUF; i++) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128 * kEP); }
         mbar_init(mdone, 1);
+        mbar_init(a4ready, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -471,6 +498,14 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer (whole warp waits, one lane issues)
+        if (KC == 2) {  // coefficient slice 4 of this CTA's cosmology tile, once
+            if (elect_one()) {
+                mbar_expect_tx(a4ready, C::kA4Bytes);
+#pragma unroll
+                for (int c = 0; c < KC; c++) tma_load_2d(sA4 + c * kM * 128, &mapA4, a4ready, c * kKC, btile * kM);
+            }
+            __syncwarp();
+        }
         uint32_t g = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < n_units; u += gridDim.x) {
@@ -500,16 +535,18 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
         // drain: every issued load has landed before the CTA may exit
         for (uint32_t h = (g > (uint32_t)kStages ? g - kStages : 0); h < g; h++)
             mbar_wait(&full[h % kStages], (h / kStages) & 1, 64);
+        if (KC == 2) mbar_wait(a4ready, 0, 64);
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer (whole warp waits; each MMA is
         // issued by one elected lane of the converged warp)
-        bool ok = __all_sync(0xffffffffu, mbar_wait(aready, 0, 64));  // coefficient slices in TMEM
-        if (!ok && lane == 0) { atomicExch(args.err, 2); *abort_flag = 1; }
+        bool ok = __all_sync(0xffffffffu, mbar_wait(aready, 0, 64) && (KC == 1 || mbar_wait(a4ready, 0, 64)));
+        if (!ok && lane == 0) { atomicExch(args.err, 2); *abort_flag = 1; }  // coefficient slices in TMEM / smem
         tc_fence_after();
         const uint32_t b0 = __shfl_sync(0xffffffffu, smem_u32(sB), 0);  // warp-uniform operands
         const uint32_t tm = __shfl_sync(0xffffffffu, tmem, 0);
         const int nk = args.Kmma / 16;        // K steps of 16
+        const uint32_t a4base = __shfl_sync(0xffffffffu, smem_u32(sA4), 0);
         const uint32_t acol = args.Kmma / 2;  // TMEM columns per coefficient slice
         uint32_t g = 0;
         for (int u = blockIdx.x; ok && u < n_units; u += gridDim.x) {
@@ -544,8 +581,13 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                                 const int p = r, q = k - r;
                                 const int lev = k < LV - 1 ? k : LV - 1;
                                 const uint32_t boff = koff + q * kBSliceBytes;
-                                umma_ts(dbase + lev * kQT, tm + C::kACol + p * acol + kk * 8,
-                                        bbase + (uint64_t)(boff >> 4), (started >> lev) & 1u);
+                                if (p < C::kSliceTmem)
+                                    umma_ts(dbase + lev * kQT, tm + C::kACol + p * acol + kk * 8,
+                                            bbase + (uint64_t)(boff >> 4), (started >> lev) & 1u);
+                                else  // slice 4 from shared memory
+                                    umma_ss(dbase + lev * kQT,
+                                            sdesc(a4base + (kk >> 2) * (kM * 128)) + (uint64_t)(((kk & 3) * 32) >> 4),
+                                            bbase + (uint64_t)(boff >> 4), (started >> lev) & 1u);
                                 started |= 1u << lev;
                             }
                         }
@@ -583,7 +625,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
             // coefficient slices of cosmology b -> TMEM lane b, columns kACol + (Kmma/2) p ..
             const int acol = args.Kmma / 2;
 #pragma unroll 1
-            for (int p = 0; p < kS; p++) {
+            for (int p = 0; p < C::kSliceTmem; p++) {
                 const uint4 *src = reinterpret_cast<const uint4 *>(args.A + ((size_t)p * args.Bpad + b) * args.Kst);
 #pragma unroll 1
                 for (int c8 = 0; c8 < acol / 8; c8++) {
@@ -734,13 +776,10 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
                             // times the tile's scale (exact); the pair (hi, lo) of tracer j at
                             // Y[t][es][a][b / 32][rt][j][hi, lo][b % 32]: a warp stores 128 bytes
                             float *y = args.Y +
-                                       (((((size_t)t * args.n_esel + es) * args.X + a) * (args.Bpad / 32) + (b >> 5)) *
-                                            args.RT + rt) * (size_t)args.MT * 64 + lane;
+                                       ((((((size_t)t * args.n_esel + es) * args.X + a) * (args.Bpad / 32) + (b >> 5)) *
+                                             args.ngr + grp) * args.RT + rt) * (size_t)kNB * 64 + lane;
 #pragma unroll
-                            for (int j = 0; j < NGB; j++) {
-                                const int jj = kNB * grp + j;
-                                if (jj < args.MT) { y[jj * 64] = Sh[j] * tsc; y[jj * 64 + 32] = Sl[j] * tsc; }
-                            }
+                            for (int j = 0; j < NGB; j++) { y[j * 64] = Sh[j] * tsc; y[j * 64 + 32] = Sl[j] * tsc; }
                         }
                     }
                 }
@@ -756,33 +795,32 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, TcArgs args)
 }
 
 // Sum over R tiles and chi nodes for the tensor-core path.  A block handles
-// (32 cosmologies, selected ell, type, A-side tracer group of five) and W
+// (32 cosmologies, selected ell, type, group of five B-side tracers) and W
 // warps split the chi nodes; a thread owns one cosmology and accumulates every
-// tracer pair (i, j) of its group:
+// tracer pair (i, j) of its group, i over all A-side tracers (MTA <= 10):
 //   s_j(a) = sum_rt Y(t, l, a, rt, j)          (pairs (hi, lo), two-sum)
 //   C_ij(l) = N_AB(l) sum_a U_i(a) s_j(a)      (exact products, two-sum)
 // Each warp streams its chi nodes through a ring of NS shared-memory stages:
-// one bulk copy brings the 32 cosmologies' R-tile pairs of a chi node
-// (contiguous in Y), another their chi weights; the chunks meet in a tree
-// through the same shared memory at the end.
-template <int MTT>
+// one bulk copy brings the 32 cosmologies' R-tile pairs of the group at a chi
+// node (contiguous in Y), another their chi weights; the chunks meet in a
+// tree through the same shared memory at the end.
+template <int MTA>
 __global__ void __launch_bounds__(256)
 k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const float *__restrict__ U, int n,
-            int X, int L, const int *__restrict__ esel, int n_esel, int RT, int MT, int nbt32, int NS,
+            int X, int L, const int *__restrict__ esel, int n_esel, int RT, int MT, int nbt32, int ngr, int NS,
             const double *__restrict__ pref, int *err)
 {
-    constexpr int NIG = MTT / kNB;  // A-side tracer groups
     extern __shared__ __align__(128) unsigned char red_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
     const int bt = blockIdx.x, es = blockIdx.y;
-    const int t = blockIdx.z / NIG, ig = blockIdx.z % NIG;
+    const int t = blockIdx.z / ngr, grp = blockIdx.z % ngr;
     const int b = bt * 32 + lane;
     const ReqDev *rq = (b < n) ? &reqs[b] : nullptr;
     const int ng = rq ? rq->n_clust : 0, ns = rq ? rq->n_lens : 0;
     const int nA = (t == 2) ? ns : ng, nB = (t == 0) ? ng : ns, kindA = (t == 2) ? 1 : 0;
     const int e = esel[es];
     const int col = rq ? rq->e_out[e] : -1;
-    const int yfl = RT * MT * 64, ufl = 2 * MT * 32, stf = yfl + ufl;  // floats per stage
+    const int yfl = RT * kNB * 64, ufl = 2 * MT * 32, stf = yfl + ufl;  // floats per stage
     float *ring = reinterpret_cast<float *>(red_smem) + (size_t)w * NS * stf;
     uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<float *>(red_smem) + (size_t)W * NS * stf) + w * NS;
     if (lane == 0) {
@@ -792,7 +830,8 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
     __syncwarp();
     const int per = (X + W - 1) / W;
     const int a0 = w * per, cnt = max(0, min(X, a0 + per) - a0);
-    const float *Yb = Y + ((size_t)t * n_esel + es) * (size_t)X * nbt32 * yfl + (size_t)bt * yfl;
+    const size_t ystride = (size_t)nbt32 * ngr * yfl;  // floats between chi nodes
+    const float *Yb = Y + ((size_t)t * n_esel + es) * (size_t)X * ystride + ((size_t)bt * ngr + grp) * yfl;
     const float *Ub = U + (size_t)bt * X * 2 * ufl + (size_t)kindA * ufl;
     auto issue = [&](int k) {  // chi node a0 + k into stage k % NS
         if (k < cnt && lane == 0) {
@@ -800,16 +839,16 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
             const int a = a0 + k;
             fence_proxy_async();
             mbar_expect_tx(&bars[k % NS], (uint32_t)stf * 4);
-            bulk_g2s(d, Yb + (size_t)a * nbt32 * yfl, (uint32_t)yfl * 4, &bars[k % NS]);
+            bulk_g2s(d, Yb + (size_t)a * ystride, (uint32_t)yfl * 4, &bars[k % NS]);
             bulk_g2s(d + yfl, Ub + (size_t)a * 2 * ufl, (uint32_t)ufl * 4, &bars[k % NS]);
         }
     };
     for (int k = 0; k < NS; k++) issue(k);
-    float Zh[kNB][MTT], Zl[kNB][MTT];
+    float Zh[MTA][kNB], Zl[MTA][kNB];
 #pragma unroll
-    for (int i = 0; i < kNB; i++)
+    for (int i = 0; i < MTA; i++)
 #pragma unroll
-        for (int j = 0; j < MTT; j++) { Zh[i][j] = 0.f; Zl[i][j] = 0.f; }
+        for (int j = 0; j < kNB; j++) { Zh[i][j] = 0.f; Zl[i][j] = 0.f; }
     int done = 0;  // chi nodes whose stage was consumed
     bool aborted = false;
     for (int k = 0; k < cnt; k++, done++) {
@@ -820,33 +859,28 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
             break;
         }
         const float *v = ring + (size_t)(k % NS) * stf;
-        float sh[MTT], sl[MTT];
+        float sv[kNB], sle[kNB];
 #pragma unroll
-        for (int j = 0; j < MTT; j++) {
-            sh[j] = 0.f;
-            sl[j] = 0.f;
-            if (j < nB) {
+        for (int j = 0; j < kNB; j++) {
+            float sh = 0.f, sl = 0.f;
+            if (kNB * grp + j < nB) {
 #pragma unroll 2
                 for (int rt = 0; rt < RT; rt++) {
-                    const float yh = v[(rt * MT + j) * 64 + lane], yl = v[(rt * MT + j) * 64 + 32 + lane];
+                    const float yh = v[(rt * kNB + j) * 64 + lane], yl = v[(rt * kNB + j) * 64 + 32 + lane];
                     float se;
-                    two_sum(sh[j], yh, sh[j], se);
-                    sl[j] = __fadd_rn(sl[j], __fadd_rn(se, yl));
+                    two_sum(sh, yh, sh, se);
+                    sl = __fadd_rn(sl, __fadd_rn(se, yl));
                 }
             }
+            two_sum(sh, sl, sv[j], sle[j]);
         }
-        float sv[MTT], sle[MTT];
-#pragma unroll
-        for (int j = 0; j < MTT; j++) two_sum(sh[j], sl[j], sv[j], sle[j]);
         const float *u = v + yfl;  // [hl][MT][32]
 #pragma unroll
-        for (int i = 0; i < kNB; i++) {
-            const int ia = kNB * ig + i;
-            if (ia >= nA) continue;
-            const float uh = u[ia * 32 + lane], ul = u[(MT + ia) * 32 + lane];
+        for (int i = 0; i < MTA; i++) {
+            if (i >= nA) continue;
+            const float uh = u[i * 32 + lane], ul = u[(MT + i) * 32 + lane];
 #pragma unroll
-            for (int j = 0; j < MTT; j++) {
-                if (j >= nB) continue;
+            for (int j = 0; j < kNB; j++) {
                 const float pr = __fmul_rn(uh, sv[j]);
                 const float pe = fmaf(uh, sle[j], fmaf(ul, sv[j], fmaf(uh, sv[j], -pr)));
                 float se;
@@ -861,27 +895,27 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
     if (aborted)
         for (int k = done; k < min(cnt, done + NS); k++) mbar_wait(&bars[k % NS], (k / NS) & 1);
     __syncthreads();  // the staging rings become the tree's exchange area
-    float *red = reinterpret_cast<float *>(red_smem);  // [W/2][32][2 kNB MTT]
-    constexpr int ZP = 2 * kNB * MTT;
+    float *red = reinterpret_cast<float *>(red_smem);  // [W/2][32][2 MTA kNB]
+    constexpr int ZP = 2 * MTA * kNB;
     for (int half = W / 2; half >= 1; half >>= 1) {
         if (w >= half && w < 2 * half) {
 #pragma unroll
-            for (int i = 0; i < kNB; i++)
+            for (int i = 0; i < MTA; i++)
 #pragma unroll
-                for (int j = 0; j < MTT; j++) {
-                    red[((w - half) * 32 + lane) * ZP + 2 * (i * MTT + j)] = Zh[i][j];
-                    red[((w - half) * 32 + lane) * ZP + 2 * (i * MTT + j) + 1] = Zl[i][j];
+                for (int j = 0; j < kNB; j++) {
+                    red[((w - half) * 32 + lane) * ZP + 2 * (i * kNB + j)] = Zh[i][j];
+                    red[((w - half) * 32 + lane) * ZP + 2 * (i * kNB + j) + 1] = Zl[i][j];
                 }
         }
         __syncthreads();
         if (w < half) {
 #pragma unroll
-            for (int i = 0; i < kNB; i++)
+            for (int i = 0; i < MTA; i++)
 #pragma unroll
-                for (int j = 0; j < MTT; j++) {
+                for (int j = 0; j < kNB; j++) {
                     float se;
-                    two_sum(Zh[i][j], red[(w * 32 + lane) * ZP + 2 * (i * MTT + j)], Zh[i][j], se);
-                    Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, red[(w * 32 + lane) * ZP + 2 * (i * MTT + j) + 1]));
+                    two_sum(Zh[i][j], red[(w * 32 + lane) * ZP + 2 * (i * kNB + j)], Zh[i][j], se);
+                    Zl[i][j] = __fadd_rn(Zl[i][j], __fadd_rn(se, red[(w * 32 + lane) * ZP + 2 * (i * kNB + j) + 1]));
                 }
         }
         __syncthreads();
@@ -890,15 +924,15 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
     const double pf = pref[t * L + e];
     const int ngg = ng * (ng + 1) / 2, ngs = ng * ns;
 #pragma unroll
-    for (int i = 0; i < kNB; i++) {
-        const int ia = kNB * ig + i;
+    for (int i = 0; i < MTA; i++) {
 #pragma unroll
-        for (int j = 0; j < MTT; j++) {
-            if (ia >= nA || j >= nB) continue;
+        for (int j = 0; j < kNB; j++) {
+            const int jb = kNB * grp + j;
+            if (i >= nA || jb >= nB) continue;
             int p;
-            if (t == 0) { if (ia > j) continue; p = ia * ng - ia * (ia - 1) / 2 + (j - ia); }
-            else if (t == 1) p = ngg + ia * ns + j;
-            else { if (ia > j) continue; p = ngg + ngs + ia * ns - ia * (ia - 1) / 2 + (j - ia); }
+            if (t == 0) { if (i > jb) continue; p = i * ng - i * (i - 1) / 2 + (jb - i); }
+            else if (t == 1) p = ngg + i * ns + jb;
+            else { if (i > jb) continue; p = ngg + ngs + i * ns - i * (i - 1) / 2 + (jb - i); }
             double out = pf * ((double)Zh[i][j] + (double)Zl[i][j]);
             if (rq->status) out = nan("");
             rq->cl[(size_t)p * rq->n_sel + col] = out;
@@ -923,6 +957,25 @@ EncodeTiledFn encode_fn()
             fn = (EncodeTiledFn)p;
     }
     return fn;
+}
+
+// 2-D map over [rows][Kst] bf16, box {64, box_rows}, 128-byte swizzle.
+int make_map2d(CUtensorMap *m, void *base, int Kst, long long rows, int box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return BLAST_EDEVICE;
+    cuuint64_t dims[2] = {(cuuint64_t)Kst, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kst * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kKC, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        blast_last_error(__FILE__, __LINE__, "cuTensorMapEncodeTiled failed");
+        return BLAST_EDEVICE;
+    }
+    return BLAST_OK;
 }
 
 // 3-D map over [S][rows][Kst] bf16, box {64, box_rows, S}, 128-byte swizzle;
@@ -953,7 +1006,8 @@ size_t tc_sa_bytes(int Bpad) { return ((size_t)Bpad * 4 + 255) / 256 * 256; }
 size_t tc_u_bytes(const blast_plan *p, int Bpad) { return (size_t)Bpad * p->X * 4 * p->max_tr * 4; }
 
 template <int KC>
-int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const TcArgs &args, cudaStream_t s)
+int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const CUtensorMap &mapA4, const TcArgs &args,
+                         cudaStream_t s)
 {
     using C = TcCfg<KC>;
     int sms = 0;
@@ -963,7 +1017,7 @@ int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const TcArgs &a
     if (grid > units) grid = units;
     if (grid < args.nbt) grid = args.nbt;
     BL_CUDA(cudaFuncSetAttribute(k_contract_tc<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem));
-    k_contract_tc<KC><<<grid, kThreads, C::kSmem, s>>>(mapB, args);
+    k_contract_tc<KC><<<grid, kThreads, C::kSmem, s>>>(mapB, mapA4, args);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
 }
@@ -980,12 +1034,13 @@ bool tc_supported(const blast_plan *p)
 
 size_t tc_y_bytes(const blast_plan *p, int n, int n_esel)
 {
-    return (size_t)3 * n_esel * p->X * bpad_of(n) * (p->Rn / kQT) * p->max_tr * 2 * 4;
+    const int ngr = (p->max_tr + kNB - 1) / kNB;
+    return (size_t)3 * n_esel * p->X * bpad_of(n) * ngr * (p->Rn / kQT) * kNB * 2 * 4;
 }
 
 int launch_basis_slices(blast_plan *p, cudaStream_t s)
 {
-    k_basis_slices<<<152 * 8, 256, 0, s>>>(p->T64, p->L, p->N, p->Q, p->Kst, p->Tsl, p->scT);
+    k_basis_slices<<<152 * 8, 256, 0, s>>>(p->T64, p->L, p->N, p->Q, p->Kst, p->Tsl, p->scT, p->d_env);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
 }
@@ -1001,7 +1056,7 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     uint16_t *A = ws.tc.as<uint16_t>();
     float *sa = reinterpret_cast<float *>(ws.tc.as<char>() + tc_a_bytes(p, Bpad));
     float *U = reinterpret_cast<float *>(ws.tc.as<char>() + tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad));
-    k_coef_slices<<<Bpad / 8, 256, 0, s>>>(dreq, n, p->N, p->Kst, Bpad, A, sa, p->X, p->max_tr, U);
+    k_coef_slices<<<Bpad / 8, 256, 0, s>>>(dreq, n, p->N, p->Kst, Bpad, A, sa, p->X, p->max_tr, U, p->d_env);
     BL_CUDA(cudaGetLastError());
 
     CUtensorMap mapB;
@@ -1028,8 +1083,13 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     args.Y = (float *)ypart;
     args.err = p->d_err;
     args.ngr = (p->max_tr + kNB - 1) / kNB;
-    if (p->Kst > kKC) return launch_contract_inst<2>(p, mapB, args, s);
-    return launch_contract_inst<1>(p, mapB, args, s);
+    if (p->Kst > kKC) {
+        // coefficient slice 4 for the shared-memory operand of the p = 4 MMAs
+        CUtensorMap mapA4;
+        if ((rc = make_map2d(&mapA4, A + (size_t)(kS - 1) * Bpad * p->Kst, p->Kst, Bpad, kM))) return rc;
+        return launch_contract_inst<2>(p, mapB, mapA4, args, s);
+    }
+    return launch_contract_inst<1>(p, mapB, mapB, args, s);
 }
 
 int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int n_esel, const void *ypart,
@@ -1038,25 +1098,24 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
     const int Bpad = bpad_of(n);
     const float *U =
         reinterpret_cast<const float *>(p->ws.tc.as<char>() + tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad));
-    const int RT = p->Rn / kQT, MT = p->max_tr;
-    const size_t stage = ((size_t)RT * MT * 64 + 2 * MT * 32) * 4;
-    // 8 warps (chi chunks), 2 for large stages, with as many stages each as fit
+    const int RT = p->Rn / kQT, MT = p->max_tr, ngr = (MT + kNB - 1) / kNB;
+    const size_t stage = ((size_t)RT * kNB * 64 + 2 * MT * 32) * 4 + 8;
+    // 8 warps (chi chunks), 4 for large stages, with as many stages each as fit
     // two blocks per SM
-    const int W = stage > 8192 ? 2 : 8;
-    int NS = (int)((110 * 1024) / (W * (stage + 8)));
+    const int W = stage > 8192 ? 4 : 8;
+    int NS = (int)((110 * 1024) / (W * stage));
     if (NS > 4) NS = 4;
     if (NS < 1) return BLAST_EINVAL;
-    const size_t smem = (size_t)W * NS * (stage + 8);
-    const bool big = MT > kNB;
-    dim3 grid(Bpad / 32, n_esel, big ? 6 : 3);
-    if (big) {
+    const size_t smem = (size_t)W * NS * stage;
+    dim3 grid(Bpad / 32, n_esel, 3 * ngr);
+    if (MT > kNB) {
         BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<2 * kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_reduce_tc<2 * kNB><<<grid, 32 * W, smem, s>>>(dreq, (const float *)ypart, U, n, p->X, p->L, d_esel,
-                                                       n_esel, RT, MT, Bpad / 32, NS, p->d_pref, p->d_err);
+                                                       n_esel, RT, MT, Bpad / 32, ngr, NS, p->d_pref, p->d_err);
     } else {
         BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_reduce_tc<kNB><<<grid, 32 * W, smem, s>>>(dreq, (const float *)ypart, U, n, p->X, p->L, d_esel, n_esel,
-                                                    RT, MT, Bpad / 32, NS, p->d_pref, p->d_err);
+                                                    RT, MT, Bpad / 32, ngr, NS, p->d_pref, p->d_err);
     }
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;

@@ -161,10 +161,10 @@ template <class T> static int dev_copy(T **dst, const std::vector<T> &src)
 
 static void plan_free_device(blast_plan *p)
 {
-    void *bufs[] = {p->d_chi, p->d_wchi, p->d_wR, p->d_kcheb_u, p->d_cos_tab, p->d_pref,
+    void *bufs[] = {p->d_chi, p->d_wchi, p->d_wR, p->d_kcheb_u, p->d_cos_tab, p->d_pref, p->d_env,
                     p->T64, p->T32, p->Tsl, p->scT};
     for (void *b : bufs) if (b) cudaFree(b);
-    p->d_chi = p->d_wchi = p->d_wR = p->d_kcheb_u = p->d_cos_tab = p->d_pref = nullptr;
+    p->d_chi = p->d_wchi = p->d_wR = p->d_kcheb_u = p->d_cos_tab = p->d_pref = p->d_env = nullptr;
     p->T64 = nullptr; p->T32 = nullptr; p->Tsl = nullptr; p->scT = nullptr;
     if (p->h_err) cudaFreeHost(p->h_err);
     p->h_err = p->d_err = nullptr;
@@ -274,7 +274,8 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
     }
     if ((rc = dev_copy(&p->d_chi, p->chi)) || (rc = dev_copy(&p->d_wchi, p->wchi)) ||
         (rc = dev_copy(&p->d_wR, p->wR)) || (rc = dev_copy(&p->d_kcheb_u, u)) ||
-        (rc = dev_copy(&p->d_cos_tab, ct)) || (rc = dev_copy(&p->d_pref, pref))) {
+        (rc = dev_copy(&p->d_cos_tab, ct)) || (rc = dev_copy(&p->d_pref, pref)) ||
+        (default_envelope(p, p->env), (rc = dev_copy(&p->d_env, p->env)))) {
         plan_free_device(p);
         delete p;
         return rc;
@@ -295,6 +296,74 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
         return rc;
     }
     *out = p;
+    return BLAST_OK;
+}
+
+// Coefficient envelope of the tensor-core path.  The slices carry 40 bits
+// relative to the largest coefficient of a cosmology; Chebyshev coefficients
+// of a power spectrum fall by three or more decades with n, so the basis row n
+// is scaled by a power of two s_n following that fall and the coefficients by
+// 1 / s_n (both exact), which spends the 40 bits on every product a_n T~_n
+// instead of on the largest a_n only.  The default s_n follows the
+// coefficients of a generic linear power spectrum shape, P(k) ~ x / (1 + x^3),
+// x = k / 0.02 h/Mpc, at the plan's Chebyshev nodes: their running maximum
+// over n +- 4, rounded to a power of two and held at or above 2^-8, because
+// tabulated spectra (spline interpolation, wiggles) keep coefficients of a
+// few 1e-3 of the largest at high n, and an envelope below a cosmology's own
+// coefficients moves its normalisation to high n and costs precision
+// everywhere.  Any positive s_n gives the same sums in exact arithmetic; a
+// poor one only costs accuracy.
+void default_envelope(const blast_plan *p, std::vector<double> &env)
+{
+    const int N = p->N;
+    std::vector<double> P(N), a(N);
+    for (int j = 0; j < N; j++) {
+        const double x = p->kcheb[j] / 0.02;
+        P[j] = x / (1.0 + x * x * x);
+    }
+    for (int n = 0; n < N; n++) {
+        double acc = 0.0;
+        for (int j = 0; j < N; j++) acc += P[j] * cos(kPi * (double)n * (2.0 * j + 1.0) / (2.0 * N));
+        a[n] = fabs((n == 0 ? 1.0 : 2.0) * acc / N);
+    }
+    double top = 0.0;
+    env.assign(N, 0.0);
+    for (int n = 0; n < N; n++) {
+        for (int m = (n > 4 ? n - 4 : 0); m <= n + 4 && m < N; m++) env[n] = fmax(env[n], a[m]);
+        top = fmax(top, env[n]);
+    }
+    for (int n = 0; n < N; n++) {
+        double r = (top > 0.0 && env[n] > 0.0) ? env[n] / top : 1.0;
+        int e = (int)lround(log2(r));
+        env[n] = ldexp(1.0, e < -8 ? -8 : (e > 0 ? 0 : e));
+    }
+}
+
+extern "C" int blast_set_coef_envelope(blast_plan *p, const double *env)
+{
+    if (!p) return BLAST_EINVAL;
+    std::vector<double> e(p->N);
+    if (env) {
+        double top = 0.0;
+        for (int n = 0; n < p->N; n++) {
+            if (!(env[n] > 0.0) || std::isinf(env[n])) return BLAST_EINVAL;
+            top = fmax(top, env[n]);
+        }
+        for (int n = 0; n < p->N; n++) {
+            int ex = (int)lround(log2(env[n] / top));
+            e[n] = ldexp(1.0, ex < -16 ? -16 : (ex > 0 ? 0 : ex));
+        }
+    } else {
+        default_envelope(p, e);
+    }
+    BL_CUDA(cudaSetDevice(p->device));
+    BL_CUDA(cudaMemcpy(p->d_env, e.data(), sizeof(double) * p->N, cudaMemcpyHostToDevice));
+    p->env = e;
+    if (p->havebf && p->Tsl) {  // rebuild the slice tables with the new envelope
+        int rc = launch_basis_slices(p, nullptr);
+        if (rc) return rc;
+        BL_CUDA(cudaStreamSynchronize(nullptr));
+    }
     return BLAST_OK;
 }
 

@@ -116,6 +116,26 @@ def test_tc_other_kernel_shapes(name):
         plan.close()
 
 
+def test_tc_coefficient_envelope(tc_case):
+    """The coefficient envelope only rescales both operands by powers of two:
+    a flat envelope, the default one and a user shape all stay within 1e-4 of
+    the oracle; a non-positive entry is refused."""
+    spec, g, T, plan = tc_case
+    rqs = [synth.config_request("tc", g.chi, g.R, i) for i in range(3)]
+    ref = [oracle_cl(g, T, rq) for rq in rqs]
+    try:
+        for env in (np.ones(spec.n_cheb), 1.0 / (1.0 + np.arange(spec.n_cheb)) ** 2, None):
+            assert bl.blast_set_coef_envelope(plan.h, env) == bl.BLAST_OK
+            outs = plan.cl_batch(rqs, bl.BLAST_BF16S)
+            for rq, C, Co in zip(rqs, outs, ref):
+                assert np.max(eij(C, Co, rq.n_clust, rq.n_lens)) < TOL
+        bad = np.ones(spec.n_cheb)
+        bad[3] = 0.0
+        assert bl.blast_set_coef_envelope(plan.h, bad) == bl.BLAST_EINVAL
+    finally:
+        bl.blast_set_coef_envelope(plan.h, None)
+
+
 def test_tc_rejects_unsupported_plan():
     spec = synth.plan_spec("tiny")  # n_R = 10 is not a multiple of 32
     plan = bl.Plan(spec)
