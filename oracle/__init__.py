@@ -62,6 +62,8 @@ def lib():
             L.orc_npairs.argtypes = [i, i]
             L.orc_cl.argtypes = [i, _ip, i, i, _dp, _dp, _dp, _dp, i, _dp, _dp, i, i,
                                  _dp, _dp, _dp, _dp, _dp, i]
+            L.orc_limber.argtypes = [i, _ip, i, _dp, _dp, i, i, _dp, _dp, _dp, i, _dp]
+            L.orc_limber_plin.argtypes = [i, _ip, i, _dp, _dp, i, _dp, _dp, _dp]
             _LIB = L
     return _LIB
 
@@ -182,6 +184,34 @@ def cl(ells, chi, wchi, R, wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, nthreads=
     return C
 
 
+# --------------------------------------------------------------------------- Limber
+def limber(ells, chi, wchi, ng, ns, kchi, Dchi, P, extended=False):
+    """Limber (or extended Limber) C[p][e] on the chi rule, P[e][a] = P(nu/chi_a, chi_a)."""
+    ells, pe = _i(ells)
+    chi, pc = _d(chi)
+    wchi, pw = _d(wchi)
+    kchi, pk = _d(kchi)
+    Dchi, pD = _d(Dchi)
+    P, pP = _d(P)
+    assert P.shape == (ells.size, chi.size), P.shape
+    C = np.empty((npairs(ng, ns), ells.size))
+    _check(lib().orc_limber(ells.size, pe, chi.size, pc, pw, ng, ns, pk, pD, pP, int(bool(extended)),
+                            _d(C)[1]), "limber")
+    return C
+
+
+def limber_plin(ells, chi, Dchi, ktab, ptab):
+    """D(chi_a)^2 P(nu/chi_a) from a P table (natural spline in (ln k, ln P)), [e][a]."""
+    ells, pe = _i(ells)
+    chi, pc = _d(chi)
+    Dchi, pD = _d(Dchi)
+    ktab, pk = _d(ktab)
+    ptab, pp = _d(ptab)
+    P = np.empty((ells.size, chi.size))
+    _check(lib().orc_limber_plin(ells.size, pe, chi.size, pc, pD, ktab.size, pk, pp, _d(P)[1]), "limber_plin")
+    return P
+
+
 # --------------------------------------------------------------------------- plan-level helpers
 class Grid:
     """The oracle's own grids for one plan description (all FP64)."""
@@ -202,6 +232,14 @@ class Grid:
 
     def fit(self, ktab, ptab):
         return fit(self.N, self.k_min, self.k_max, ktab, ptab, self.k_map)
+
+    def limber(self, ng, ns, kchi, Dchi, P, extended=False, ell_subset=None):
+        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
+        return limber(ells, self.chi, self.wchi, ng, ns, kchi, Dchi, P, extended)
+
+    def limber_plin(self, Dchi, ktab, ptab, ell_subset=None):
+        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
+        return limber_plin(ells, self.chi, Dchi, ktab, ptab)
 
     def cl(self, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, ell_subset=None, nthreads=0):
         ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
