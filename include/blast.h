@@ -190,6 +190,36 @@ int blast_cl(blast_plan *plan, const blast_request *req, int precision,
 int blast_cl_batch(blast_plan *plan, int n, const blast_request *reqs, int precision,
                    double *const *outs, int out_mem_space, void *stream);
 
+/* ---------------------------------------------------------------- Limber
+ * The Limber approximation of Sec. 2.2 on the plan's chi rule,
+ *   C^Limber_ij(l) = pref_AB(l) sum_a wchi_a / chi_a^2 W_i(chi_a) W_j(chi_a) P(nu / chi_a, chi_a),
+ * nu = l + 1/2, pref = 1 (gg), sqrt((l+2)(l+1)l(l-1)) / nu^2 (gs),
+ * (l+2)(l+1)l(l-1) / nu^4 (ss), W = the clustering kernel, or the lensing
+ * kernel times chi^2 (requests carry lensing kernels divided by chi^2).
+ *
+ * blast_limber_k: the Limber points k[e][a] = (ell_e + 1/2) / chi_a,
+ *   [n_ell][n_chi] host doubles, at which a caller samples its non-linear P.
+ * blast_cl_limber: C^Limber for one request (no basis needed), cl_out as
+ *   blast_cl.  p_nl NULL: the request's linear spectrum, D(chi_a)^2 P(k) with
+ *   P(k) from its table by the natural cubic spline in (ln k, ln P) of the
+ *   Chebyshev fit, zero outside the table; extended = 1 adds the first-order
+ *   (extended Limber) correction: each term times
+ *   1 - [chi^2/2 (Kt_i''/Kt_i + Kt_j''/Kt_j) + chi^3/6 (Kt_i'''/Kt_i + Kt_j'''/Kt_j)] / nu^2,
+ *   Kt = W D / sqrt(chi), derivatives by central differences on the chi nodes
+ *   (needs n_chi >= 5).  p_nl set: P[e][a] at the Limber points for every
+ *   plan ell, [n_ell][n_chi] doubles in the request's memory space, used as
+ *   given (growth included by the caller); extended must then be 0.
+ * blast_cl_nonlinear: the total spectrum of Sec. 3.2,
+ *   C_tot = C_lin + C^Limber(P_delta) - C^Limber(P_lin),
+ *   C_lin the beyond-Limber C_l at `precision`, p_nl = P_delta at the Limber
+ *   points as above; the correction vanishes when p_nl holds the linear P.
+ * Errors as blast_cl (BLAST_EINVAL also for a misaligned p_nl). */
+int blast_limber_k(const blast_plan *plan, double *k);
+int blast_cl_limber(blast_plan *plan, const blast_request *req, const double *p_nl, int extended, double *cl_out,
+                    int out_mem_space, void *stream);
+int blast_cl_nonlinear(blast_plan *plan, const blast_request *req, int precision, const double *p_nl,
+                       double *cl_out, int out_mem_space, void *stream);
+
 /* Coefficient envelope of BLAST_BF16S.  The five slices hold each cosmology's
  * Chebyshev coefficients to 40 bits of its largest one; since the coefficients
  * of a power spectrum fall by decades with n, basis row n is scaled by a power
@@ -289,6 +319,15 @@ int blast_server_destroy(blast_server *server);
 int blast_profile_enable(blast_plan *plan, int enable);
 int blast_profile_read(blast_plan *plan, int kernel_class, double *total_ms, long long *launches);
 int blast_profile_reset(blast_plan *plan);
+
+/* Test hook of the bounded device waits.  The next BLAST_BF16S call on the
+ * plan has one epilogue warp of its first CTA wait, before tile `tile`, on a
+ * barrier that nothing completes, with a limit of 2e7 clock cycles; the wait
+ * runs out, the kernel records the error word and every warp leaves after its
+ * copies and MMAs in flight complete, and the call returns BLAST_ETIMEOUT (a
+ * host-output call at once, a device-output call on the next call).  The
+ * context stays usable; -1 cancels.  Errors: BLAST_EINVAL. */
+int blast_test_trip_wait(blast_plan *plan, int tile);
 
 /* Human-readable name of a status code (static string). */
 const char *blast_status_str(int status);

@@ -84,6 +84,10 @@ def lib():
             L.blast_status_str.restype = ctypes.c_char_p
             L.blast_cl_noalloc.argtypes = [P, ctypes.POINTER(blast_request), P, P]
             L.blast_set_coef_envelope.argtypes = [P, P]
+            L.blast_limber_k.argtypes = [P, _dp]
+            L.blast_test_trip_wait.argtypes = [P, i]
+            L.blast_cl_limber.argtypes = [P, ctypes.POINTER(blast_request), P, i, P, i, P]
+            L.blast_cl_nonlinear.argtypes = [P, ctypes.POINTER(blast_request), i, P, P, i, P]
             L.blast_profile_enable.argtypes = [P, i]
             L.blast_profile_read.argtypes = [P, i, _dp, ctypes.POINTER(ctypes.c_longlong)]
             L.blast_profile_reset.argtypes = [P]
@@ -142,6 +146,24 @@ def blast_cl_noalloc(h, req, out_ptr, stream=None):
     """FP64 C_l of one cosmology without any device allocation (device inputs
     and output); scratch comes from a fixed array inside the library."""
     return lib().blast_cl_noalloc(h, ctypes.byref(req), out_ptr, stream)
+
+
+def blast_test_trip_wait(h, tile):
+    return lib().blast_test_trip_wait(h, tile)
+
+
+def blast_limber_k(h, L, X):
+    k = np.empty((L, X))
+    _check(lib().blast_limber_k(h, k.ctypes.data_as(_dp)), "blast_limber_k")
+    return k
+
+
+def blast_cl_limber(h, req, p_nl_ptr, extended, out_ptr, out_mem_space, stream=None):
+    return lib().blast_cl_limber(h, ctypes.byref(req), p_nl_ptr, extended, out_ptr, out_mem_space, stream)
+
+
+def blast_cl_nonlinear(h, req, precision, p_nl_ptr, out_ptr, out_mem_space, stream=None):
+    return lib().blast_cl_nonlinear(h, ctypes.byref(req), precision, p_nl_ptr, out_ptr, out_mem_space, stream)
 
 
 def blast_set_coef_envelope(h, env=None):
@@ -300,6 +322,23 @@ class Plan:
         r = self.request(rq, ell_sel)
         out = np.empty((blast_npairs(rq.n_clust, rq.n_lens), self.n_sel(ell_sel)))
         _check(blast_cl(self.h, r, precision, out.ctypes.data, 0), "blast_cl")
+        return out
+
+    def limber(self, rq, p_nl=None, extended=False, ell_sel=None):
+        """C^Limber (host arrays): the request's linear P, or p_nl[n_ell][n_chi]."""
+        r = self.request(rq, ell_sel)
+        out = np.empty((blast_npairs(rq.n_clust, rq.n_lens), self.n_sel(ell_sel)))
+        pn = None if p_nl is None else np.ascontiguousarray(p_nl, dtype=np.float64)
+        _check(blast_cl_limber(self.h, r, None if pn is None else pn.ctypes.data, int(bool(extended)),
+                               out.ctypes.data, 0), "blast_cl_limber")
+        return out
+
+    def nonlinear(self, rq, p_nl, precision=BLAST_FP64, ell_sel=None):
+        """C_tot = C_lin + C^Limber(P_delta) - C^Limber(P_lin) (host arrays)."""
+        r = self.request(rq, ell_sel)
+        out = np.empty((blast_npairs(rq.n_clust, rq.n_lens), self.n_sel(ell_sel)))
+        pn = np.ascontiguousarray(p_nl, dtype=np.float64)
+        _check(blast_cl_nonlinear(self.h, r, precision, pn.ctypes.data, out.ctypes.data, 0), "blast_cl_nonlinear")
         return out
 
     def cl_batch(self, rqs, precision=BLAST_FP64, ell_sels=None):

@@ -43,6 +43,7 @@ struct Workspace {
     DevBuf cl;      // device C before scatter to the caller
     DevBuf meta;    // per-request descriptors
     DevBuf tc;      // coefficient slices and scales of the tensor-core path
+    DevBuf nl;      // non-linear spectra at the Limber points, staged from host requests
     std::vector<char> hmeta;
 };
 
@@ -63,6 +64,7 @@ struct blast_plan {
     double *d_kcheb_u = nullptr;   // ln k of each Chebyshev node
     double *d_cos_tab = nullptr;   // cos(pi p / 2N), p < 4N
     double *d_pref = nullptr;      // N_AB(l) [3][L]
+    int32_t *d_ell = nullptr;      // the plan's ells
     std::vector<double> env;       // power-of-two coefficient envelope s_n of the tensor-core path
     double *d_env = nullptr;
 
@@ -75,6 +77,7 @@ struct blast_plan {
     int Kst = 0;                    // stored K of the slice table: max(64, Kmma), zero padded
     bool have64 = false, have32 = false, havebf = false;
     int *d_err = nullptr;           // host-mapped error word written by bounded device waits
+    int test_trip = -1;             // test hook of the tensor-core contraction (blast_test_trip_wait)
     int *h_err = nullptr;
 
     Workspace ws;
@@ -114,6 +117,8 @@ struct ReqDev {
     double *U64, *V64;  // [ntr][X], [ntr][Q]
     float *U32, *V32;
     double *cl;       // [npairs][n_sel] device output
+    double *spM;      // [n_ptab] spline second derivatives of ln P (ln k), written by the fit if set
+    const double *pnl;  // [L][X] non-linear P at the Limber points (Limber paths), or null
     int n_sel;
     int e_out[BLAST_MAX_ELL];  // plan ell e -> output column, -1 if not selected
 };
@@ -132,6 +137,11 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int nreq, const int *d_esel,
 int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int nreq, const int *d_esel, int n_esel,
                      const void *ypart, cudaStream_t s);
 int launch_basis_slices(blast_plan *p, cudaStream_t s);
+// Limber terms (limber.cu): mode 0 writes C^Limber with the linear P of each
+// request (extended adds the first-order correction), mode 1 writes it with
+// the request's non-linear table, mode 2 adds C^Limber(P_nl) - C^Limber(P_lin).
+int launch_limber(blast_plan *p, ReqDev *dreq, int nreq, const int *d_esel, int n_esel, int mode, int extended,
+                  cudaStream_t s);
 bool tc_supported(const blast_plan *p);
 size_t tc_y_bytes(const blast_plan *p, int n, int n_esel);  // R-tile partials of a tensor-core call
 

@@ -132,12 +132,13 @@ __device__ __forceinline__ void named_bar_sync(int id, int n)
 // cycles.  With sleep_ns > 0 the thread sleeps between tests, doubling up to
 // 1 us: for the TMA and MMA warps, which wait most of the time and need not
 // answer within a few cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned sleep_ns = 0)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned sleep_ns = 0,
+                                          long long limit = kWaitLimit)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitLimit) return false;
+        if (clock64() - t0 > limit) return false;
         if (sleep_ns) {
             __nanosleep(sleep_ns);
             sleep_ns = min(2u * sleep_ns, 1024u);
@@ -438,6 +439,7 @@ struct TcArgs {
     const uint16_t *A;   // [S][Bpad][Kst] coefficient slices
     float *Y;            // [3][n_esel][X][Bpad/32][ngr][RT][5][hi, lo][32] R-tile partial pairs
     int *err;            // host-mapped error word
+    int trip;            // test hook: tile at which CTA 0 waits on a barrier nothing completes (-1 off)
 };
 
 // Work units: (cosmology tile, group of five B-side tracers, 32-column q
@@ -466,7 +468,8 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
     uint64_t *bars = (uint64_t *)(sA4 + C::kA4Bytes);                   // kCtrlBytes of control words
     uint64_t *full = bars, *empty = bars + kStages, *aready = bars + 2 * kStages;
     uint64_t *tfull = aready + 1, *tempty = tfull + kNBUF, *mdone = tempty + kNBUF, *a4ready = mdone + 1;
-    uint32_t *tmem_slot = (uint32_t *)(a4ready + 1);
+    uint64_t *never = a4ready + 1;  // no thread ever arrives on it (test hook)
+    uint32_t *tmem_slot = (uint32_t *)(never + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     int *s_esel = (int *)((unsigned char *)bars + kCtrlBytes);         // selected ells
     float *ybuf = (float *)((unsigned char *)s_esel + kEselBytes);     // [2][4][NGB][2][32] column-half hand-over
@@ -482,6 +485,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
         for (int i = 0; i < kNBUF; i++) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128 * kEP); }
         mbar_init(mdone, 1);
         mbar_init(a4ready, 1);
+        mbar_init(never, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -677,6 +681,14 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
                         (part == 0) ? args.scT[((size_t)t * args.L + s_esel[es]) * (args.Q / kQT) + q0 / kQT] : 0.f;
                     if (!dead) {
                         bool lost = *abort_flag != 0;
+                        // test hook: one warp of CTA 0 waits, with a 20M-cycle limit, on a
+                        // barrier nothing completes, so the bounded wait runs out
+                        if (!lost && (int)g == args.trip && blockIdx.x == 0 && warp == 2 &&
+                            !mbar_wait(never, 0, 0, 20000000LL)) {
+                            lost = true;
+                            atomicExch(args.err, 4);
+                            *abort_flag = 1;
+                        }
                         if (!lost && !mbar_wait(&tfull[buf], tph)) {
                             lost = true;
                             atomicExch(args.err, 4);
@@ -1082,6 +1094,8 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     args.A = A;
     args.Y = (float *)ypart;
     args.err = p->d_err;
+    args.trip = p->test_trip;
+    p->test_trip = -1;  // one call only
     args.ngr = (p->max_tr + kNB - 1) / kNB;
     if (p->Kst > kKC) {
         // coefficient slice 4 for the shared-memory operand of the p = 4 MMAs

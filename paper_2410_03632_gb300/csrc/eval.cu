@@ -94,7 +94,10 @@ k_fit(ReqDev *reqs, int N, const double *__restrict__ node_u, const double *__re
         t = a; a = a2; a2 = t; t = b; b = b2; b2 = t; t = c; c = c2; c2 = t; t = d; d = d2; d2 = t;
     }
     double *M = a2;  // reuse a free buffer
-    for (int i = tid; i < n; i += blockDim.x) M[i] = d[i] / b[i];
+    for (int i = tid; i < n; i += blockDim.x) {
+        M[i] = d[i] / b[i];
+        if (rq.spM) rq.spM[i] = M[i];  // kept for the Limber terms
+    }
     __syncthreads();
     // spline at the Chebyshev nodes, then exp
     for (int j = tid; j < N; j += blockDim.x) {
@@ -395,7 +398,7 @@ static const void *device_view(const void *hp, int pageable)
 
 int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, double *const *outs,
                 int out_mem_space, cudaStream_t s, ReqDev **dreq_out, int **d_esel, int *n_esel,
-                std::vector<ReqDev> &hreq, std::vector<char> &direct_out)
+                std::vector<ReqDev> &hreq, std::vector<char> &direct_out, const double *const *pnl = nullptr)
 {
     Workspace &ws = p->ws;
     int pageable = 0;
@@ -415,7 +418,9 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
     // request's double / float arrays stay aligned
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     size_t in_per = al(request_in_doubles(p, ntr_max, kMaxPtab) * 8) / 8;
-    size_t coef_per = al((size_t)p->N * 8) + al((size_t)p->N * 4);
+    // coefficients (FP64, FP32) and the spline second derivatives the Limber terms use
+    size_t coef_per = al((size_t)p->N * 8) + al((size_t)p->N * 4) + al((size_t)kMaxPtab * 8);
+    const size_t nl_per = al((size_t)p->L * p->X * 8);  // staged non-linear tables (host requests)
     size_t u64 = al((size_t)ntr_max * p->X * 8), v64 = al((size_t)ntr_max * p->Q * 8);
     size_t u32 = al((size_t)ntr_max * p->X * 4), v32 = al((size_t)ntr_max * p->Q * 4);
     size_t wts_per = u64 + v64 + u32 + v32;
@@ -429,6 +434,7 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
         (rc = ws.meta.ensure(sizeof(ReqDev) * n + sizeof(int) * BLAST_MAX_ELL)))
         return rc;
     if (out_mem_space == 0 && (rc = ws.cl.ensure(cl_per * 8 * n))) return rc;
+    if (pnl && any_host_in && (rc = ws.nl.ensure(nl_per * n))) return rc;
 
     hreq.resize(n);
     char *coef = ws.coef.as<char>(), *wts = ws.wts.as<char>();
@@ -468,6 +474,15 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
         char *c = coef + coef_per * i;
         h.a64 = (double *)c;
         h.a32 = (float *)(c + al((size_t)p->N * 8));
+        h.spM = (double *)(c + al((size_t)p->N * 8) + al((size_t)p->N * 4));
+        if (pnl && pnl[i]) {
+            if (r.mem_space == 1) h.pnl = pnl[i];
+            else {
+                double *dst = (double *)(ws.nl.as<char>() + nl_per * i);
+                BL_CUDA(cudaMemcpyAsync(dst, pnl[i], sizeof(double) * p->L * p->X, cudaMemcpyHostToDevice, s));
+                h.pnl = dst;
+            }
+        }
         char *w = wts + wts_per * i;
         h.U64 = (double *)w;
         h.V64 = (double *)(w + u64);
@@ -512,8 +527,12 @@ int finish_batch(blast_plan *p, int n, const std::vector<ReqDev> &hreq, const st
     return BLAST_OK;
 }
 
-extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, int prec, double *const *outs,
-                              int out_mem_space, void *stream)
+// One pass over a batch.  lmode 0: beyond-Limber C_l (steps a0, a, b);
+// lmode 1: the Limber integral only (no basis), with each request's linear P
+// or, when pnl[i] is set, its non-linear table; lmode 2: beyond-Limber C_l
+// plus the non-linear correction C^Limber(P_delta) - C^Limber(P_lin).
+static int cl_impl(blast_plan *p, int n, const blast_request *reqs, int prec, double *const *outs, int out_mem_space,
+                   void *stream, const double *const *pnl, int lmode, int extended)
 {
     if (!p || n < 1 || !reqs || !outs) return BLAST_EINVAL;
     if (prec < BLAST_FP64 || prec > BLAST_BF16S) return BLAST_EINVAL;
@@ -522,12 +541,16 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
         int rc = validate_request(p, &reqs[i]);
         if (rc) return rc;
         if (!outs[i]) return BLAST_EINVAL;
+        if (pnl && pnl[i] && reinterpret_cast<uintptr_t>(pnl[i]) % 8) return BLAST_EINVAL;
     }
-    const bool use_tc = (prec == BLAST_BF16S);
-    if (use_tc && !tc_supported(p)) return BLAST_EINVAL;
-    if (prec == BLAST_FP64 && !p->have64) return BLAST_ENOBASIS;
-    if (prec == BLAST_FP32 && !p->have32) return BLAST_ENOBASIS;
-    if (use_tc && !p->havebf) return BLAST_ENOBASIS;
+    if (extended && (lmode != 1 || p->X < 5 || (pnl && pnl[0]))) return BLAST_EINVAL;
+    const bool use_tc = (prec == BLAST_BF16S) && lmode != 1;
+    if (lmode != 1) {
+        if (use_tc && !tc_supported(p)) return BLAST_EINVAL;
+        if (prec == BLAST_FP64 && !p->have64) return BLAST_ENOBASIS;
+        if (prec == BLAST_FP32 && !p->have32) return BLAST_ENOBASIS;
+        if (use_tc && !p->havebf) return BLAST_ENOBASIS;
+    }
     if (*p->h_err) {  // a bounded device wait of an earlier call gave up
         *p->h_err = 0;
         return BLAST_ETIMEOUT;
@@ -538,9 +561,15 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
     int *d_esel = nullptr, n_esel = 0;
     std::vector<ReqDev> hreq;
     std::vector<char> direct_out;
-    int rc = stage_batch(p, n, reqs, prec, outs, out_mem_space, s, &dreq, &d_esel, &n_esel, hreq, direct_out);
+    int rc = stage_batch(p, n, reqs, lmode == 1 ? BLAST_FP64 : prec, outs, out_mem_space, s, &dreq, &d_esel, &n_esel,
+                         hreq, direct_out, pnl);
     if (rc) return rc;
-    if (use_tc) {
+    if (lmode == 1) {
+        if ((rc = prof_launch(p, BLAST_K_REDUCE, s, [&] {
+                 return launch_limber(p, dreq, n, d_esel, n_esel, (pnl && pnl[0]) ? 1 : 0, extended, s);
+             })))
+            return rc;
+    } else if (use_tc) {
         const size_t ybytes = tc_y_bytes(p, n, n_esel);
         if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
         if ((rc = prof_launch(p, BLAST_K_CONTRACT_TC, s, [&] {
@@ -563,6 +592,10 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
              })))
             return rc;
     }
+    if (lmode == 2 && (rc = prof_launch(p, BLAST_K_REDUCE, s, [&] {
+                           return launch_limber(p, dreq, n, d_esel, n_esel, 2, 0, s);
+                       })))
+        return rc;
     rc = finish_batch(p, n, hreq, direct_out, outs, out_mem_space, s);
     if (!rc && out_mem_space == 0 && *p->h_err) {
         *p->h_err = 0;
@@ -571,12 +604,51 @@ extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, i
     return rc;
 }
 
+extern "C" int blast_cl_batch(blast_plan *p, int n, const blast_request *reqs, int prec, double *const *outs,
+                              int out_mem_space, void *stream)
+{
+    return cl_impl(p, n, reqs, prec, outs, out_mem_space, stream, nullptr, 0, 0);
+}
+
 extern "C" int blast_cl(blast_plan *p, const blast_request *req, int prec, double *cl_out, int out_mem_space,
                         void *stream)
 {
     if (!req || !cl_out) return BLAST_EINVAL;
     double *outs[1] = {cl_out};
     return blast_cl_batch(p, 1, req, prec, outs, out_mem_space, stream);
+}
+
+extern "C" int blast_test_trip_wait(blast_plan *p, int tile)
+{
+    if (!p || tile < -1) return BLAST_EINVAL;
+    p->test_trip = tile;
+    return BLAST_OK;
+}
+
+extern "C" int blast_limber_k(const blast_plan *p, double *k)
+{
+    if (!p || !k) return BLAST_EINVAL;
+    for (int e = 0; e < p->L; e++)
+        for (int a = 0; a < p->X; a++) k[(size_t)e * p->X + a] = ((double)p->ell[e] + 0.5) / p->chi[a];
+    return BLAST_OK;
+}
+
+extern "C" int blast_cl_limber(blast_plan *p, const blast_request *req, const double *p_nl, int extended,
+                               double *cl_out, int out_mem_space, void *stream)
+{
+    if (!req || !cl_out || (extended != 0 && extended != 1)) return BLAST_EINVAL;
+    double *outs[1] = {cl_out};
+    const double *nl[1] = {p_nl};
+    return cl_impl(p, 1, req, BLAST_FP64, outs, out_mem_space, stream, nl, 1, extended);
+}
+
+extern "C" int blast_cl_nonlinear(blast_plan *p, const blast_request *req, int prec, const double *p_nl,
+                                  double *cl_out, int out_mem_space, void *stream)
+{
+    if (!req || !cl_out || !p_nl) return BLAST_EINVAL;
+    double *outs[1] = {cl_out};
+    const double *nl[1] = {p_nl};
+    return cl_impl(p, 1, req, prec, outs, out_mem_space, stream, nl, 2, 0);
 }
 
 extern "C" int blast_profile_enable(blast_plan *p, int enable)

@@ -161,15 +161,16 @@ template <class T> static int dev_copy(T **dst, const std::vector<T> &src)
 
 static void plan_free_device(blast_plan *p)
 {
-    void *bufs[] = {p->d_chi, p->d_wchi, p->d_wR, p->d_kcheb_u, p->d_cos_tab, p->d_pref, p->d_env,
+    void *bufs[] = {p->d_chi, p->d_wchi, p->d_wR, p->d_kcheb_u, p->d_cos_tab, p->d_pref, p->d_env, p->d_ell,
                     p->T64, p->T32, p->Tsl, p->scT};
     for (void *b : bufs) if (b) cudaFree(b);
     p->d_chi = p->d_wchi = p->d_wR = p->d_kcheb_u = p->d_cos_tab = p->d_pref = p->d_env = nullptr;
+    p->d_ell = nullptr;
     p->T64 = nullptr; p->T32 = nullptr; p->Tsl = nullptr; p->scT = nullptr;
     if (p->h_err) cudaFreeHost(p->h_err);
     p->h_err = p->d_err = nullptr;
     p->ws.in.release(); p->ws.coef.release(); p->ws.wts.release();
-    p->ws.ypart.release(); p->ws.cl.release(); p->ws.meta.release(); p->ws.tc.release();
+    p->ws.ypart.release(); p->ws.cl.release(); p->ws.meta.release(); p->ws.tc.release(); p->ws.nl.release();
 }
 
 extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
@@ -274,7 +275,7 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
     }
     if ((rc = dev_copy(&p->d_chi, p->chi)) || (rc = dev_copy(&p->d_wchi, p->wchi)) ||
         (rc = dev_copy(&p->d_wR, p->wR)) || (rc = dev_copy(&p->d_kcheb_u, u)) ||
-        (rc = dev_copy(&p->d_cos_tab, ct)) || (rc = dev_copy(&p->d_pref, pref)) ||
+        (rc = dev_copy(&p->d_cos_tab, ct)) || (rc = dev_copy(&p->d_pref, pref)) || (rc = dev_copy(&p->d_ell, p->ell)) ||
         (default_envelope(p, p->env), (rc = dev_copy(&p->d_env, p->env)))) {
         plan_free_device(p);
         delete p;
