@@ -63,6 +63,7 @@ def lib():
             L.orc_cl.argtypes = [i, _ip, i, i, _dp, _dp, _dp, _dp, i, _dp, _dp, i, i,
                                  _dp, _dp, _dp, _dp, _dp, i]
             L.orc_limber.argtypes = [i, _ip, i, _dp, _dp, i, i, _dp, _dp, _dp, i, _dp]
+            L.orc_cl_nonsep.argtypes = [i, _ip, i, i, _dp, _dp, _dp, i, _dp, _dp, i, i, _dp, _dp, _dp]
             L.orc_limber_plin.argtypes = [i, _ip, i, _dp, _dp, i, _dp, _dp, _dp]
             _LIB = L
     return _LIB
@@ -212,6 +213,25 @@ def limber_plin(ells, chi, Dchi, ktab, ptab):
     return P
 
 
+def cl_nonsep(ells, chi, wchi, wR, T, Pq, ng, ns, kchi, kRchi):
+    """C[p][e] for a non-separable P sampled at the Chebyshev k-nodes of every
+    chi-R node, Pq[q][j] (q = a n_R + r)."""
+    ells, pe = _i(ells)
+    chi, pc = _d(chi)
+    wchi, pw = _d(wchi)
+    wR, pwR = _d(wR)
+    T, pT = _d(T)
+    Pq, pP = _d(Pq)
+    kchi, pk = _d(kchi)
+    kRchi, pkR = _d(kRchi)
+    X, Rn, N = chi.size, wR.size, Pq.shape[1]
+    assert T.shape == (3, ells.size, N, X * Rn) and Pq.shape == (X * Rn, N)
+    C = np.empty((npairs(ng, ns), ells.size))
+    _check(lib().orc_cl_nonsep(ells.size, pe, X, Rn, pc, pw, pwR, N, pT, pP, ng, ns, pk, pkR, _d(C)[1]),
+           "cl_nonsep")
+    return C
+
+
 # --------------------------------------------------------------------------- plan-level helpers
 class Grid:
     """The oracle's own grids for one plan description (all FP64)."""
@@ -232,6 +252,10 @@ class Grid:
 
     def fit(self, ktab, ptab):
         return fit(self.N, self.k_min, self.k_max, ktab, ptab, self.k_map)
+
+    def cl_nonsep(self, T, Pq, ng, ns, kchi, kRchi, ell_subset=None):
+        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
+        return cl_nonsep(ells, self.chi, self.wchi, self.wR, T, Pq, ng, ns, kchi, kRchi)
 
     def limber(self, ng, ns, kchi, Dchi, P, extended=False, ell_subset=None):
         ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)

@@ -595,3 +595,56 @@ int orc_limber_plin(int n_ell, const int *ell, int X, const double *chi, const d
     free(u); free(v); free(uq); free(out);
     return rc;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Non-separable spectrum (Eqs. cheb_pk, pmd with general c_n(chi1, chi2)).  */
+/* Pq[q][j] = P(k_j, chi_a, R_r chi_a) at the N Chebyshev k-nodes for every  */
+/* chi-R node q = a Rn + r; per node the coefficients follow from the        */
+/* transform of orc_cheb_dct, c_n(q), and                                    */
+/*   w_l(a, r) = sum_n c_n(q) T~_{n;l}(a, r)                                 */
+/* replaces D(chi_a) D(R_r chi_a) sum_n a_n T~; the chi-R quadrature is that */
+/* of orc_cl with the kernels K alone.  Output C[p][e].                      */
+/* ------------------------------------------------------------------------- */
+int orc_cl_nonsep(int n_ell, const int *ell, int X, int Rn, const double *chi, const double *wchi,
+                  const double *wR, int N, const double *T, const double *Pq, int ng, int ns,
+                  const double *kchi, const double *kRchi, double *C)
+{
+    if (n_ell < 1 || X < 1 || Rn < 1 || N < 1 || ng < 0 || ns < 0 || ng + ns < 1) return -1;
+    const int Q = X * Rn;
+    double *c = (double *)malloc(sizeof(double) * (size_t)Q * N);
+    double *w = (double *)malloc(sizeof(double) * Q);
+    if (!c || !w) { free(c); free(w); return -2; }
+    int rc = 0;
+    for (int q = 0; !rc && q < Q; q++) rc = orc_cheb_dct(N, Pq + (size_t)q * N, c + (size_t)q * N);
+    int p0[3] = {0, ng * (ng + 1) / 2, ng * (ng + 1) / 2 + ng * ns};
+    for (int t = 0; !rc && t < 3; t++) {
+        for (int e = 0; e < n_ell; e++) {
+            const double *Te = T + ((size_t)t * n_ell + e) * N * (size_t)Q;
+            for (int q = 0; q < Q; q++) {
+                double s = 0.0;
+                for (int n = 0; n < N; n++) s += c[(size_t)q * N + n] * Te[(size_t)n * Q + q];
+                w[q] = s;
+            }
+            double pref = orc_prefactor(t, ell[e]);
+            int p = p0[t];
+            int nA = (t == 2) ? ns : ng, nB = (t == 0) ? ng : ns;
+            int offA = (t == 2) ? ng : 0, offB = (t == 0) ? 0 : ng;
+            for (int i = 0; i < nA; i++) {
+                for (int j = (t == 1 ? 0 : i); j < nB; j++) {
+                    const double *Ki = kchi + (size_t)(offA + i) * X;
+                    const double *Kj = kRchi + (size_t)(offB + j) * Q;
+                    double s = 0.0;
+                    for (int aa = 0; aa < X; aa++) {
+                        double sr = 0.0;
+                        for (int r = 0; r < Rn; r++) sr += wR[r] * Kj[aa * Rn + r] * w[aa * Rn + r];
+                        s += wchi[aa] * chi[aa] * Ki[aa] * sr;
+                    }
+                    C[(size_t)p * n_ell + e] = pref * s;
+                    p++;
+                }
+            }
+        }
+    }
+    free(c); free(w);
+    return rc;
+}
