@@ -190,6 +190,19 @@ int blast_cl(blast_plan *plan, const blast_request *req, int precision,
 int blast_cl_batch(blast_plan *plan, int n, const blast_request *reqs, int precision,
                    double *const *outs, int out_mem_space, void *stream);
 
+/* Non-separable spectrum (Eqs. cheb_pk and pmd with a general c_n(chi1, chi2):
+ * scale-dependent growth, massive neutrinos).  p_nodes[q][j] = P(k_j, chi_a,
+ * R_r chi_a) at the Chebyshev k-nodes k_j of blast_plan_nodes for every chi-R
+ * node q = a n_R + r, [n_chi n_R][n_cheb] doubles in the request's memory
+ * space.  Per node the coefficients are fitted in FP64 on the device (the
+ * transform of the separable fit), w_l = sum_n c_n(q) T~_{n;l}(q), and the
+ * chi-R quadrature is the FP64 one.  The request's growth arrays still
+ * multiply the kernels (pass ones when p_nodes carries the whole time
+ * dependence); its P table is checked as for blast_cl but not used.
+ * cl_out as blast_cl.  Errors as blast_cl. */
+int blast_cl_nonsep(blast_plan *plan, const blast_request *req, const double *p_nodes, double *cl_out,
+                    int out_mem_space, void *stream);
+
 /* ---------------------------------------------------------------- Limber
  * The Limber approximation of Sec. 2.2 on the plan's chi rule,
  *   C^Limber_ij(l) = pref_AB(l) sum_a wchi_a / chi_a^2 W_i(chi_a) W_j(chi_a) P(nu / chi_a, chi_a),

@@ -85,6 +85,7 @@ def lib():
             L.blast_cl_noalloc.argtypes = [P, ctypes.POINTER(blast_request), P, P]
             L.blast_set_coef_envelope.argtypes = [P, P]
             L.blast_limber_k.argtypes = [P, _dp]
+            L.blast_cl_nonsep.argtypes = [P, ctypes.POINTER(blast_request), P, P, i, P]
             L.blast_test_trip_wait.argtypes = [P, i]
             L.blast_cl_limber.argtypes = [P, ctypes.POINTER(blast_request), P, i, P, i, P]
             L.blast_cl_nonlinear.argtypes = [P, ctypes.POINTER(blast_request), i, P, P, i, P]
@@ -150,6 +151,10 @@ def blast_cl_noalloc(h, req, out_ptr, stream=None):
 
 def blast_test_trip_wait(h, tile):
     return lib().blast_test_trip_wait(h, tile)
+
+
+def blast_cl_nonsep(h, req, p_nodes_ptr, out_ptr, out_mem_space, stream=None):
+    return lib().blast_cl_nonsep(h, ctypes.byref(req), p_nodes_ptr, out_ptr, out_mem_space, stream)
 
 
 def blast_limber_k(h, L, X):
@@ -331,6 +336,16 @@ class Plan:
         pn = None if p_nl is None else np.ascontiguousarray(p_nl, dtype=np.float64)
         _check(blast_cl_limber(self.h, r, None if pn is None else pn.ctypes.data, int(bool(extended)),
                                out.ctypes.data, 0), "blast_cl_limber")
+        return out
+
+    def nonsep(self, rq, p_nodes, ell_sel=None):
+        """Beyond-Limber C_l of a non-separable P sampled at the Chebyshev k-nodes of
+        every chi-R node, p_nodes[n_chi * n_R][n_cheb] (host arrays)."""
+        r = self.request(rq, ell_sel)
+        out = np.empty((blast_npairs(rq.n_clust, rq.n_lens), self.n_sel(ell_sel)))
+        pn = np.ascontiguousarray(p_nodes, dtype=np.float64)
+        assert pn.shape == (self.Q, self.N)
+        _check(blast_cl_nonsep(self.h, r, pn.ctypes.data, out.ctypes.data, 0), "blast_cl_nonsep")
         return out
 
     def nonlinear(self, rq, p_nl, precision=BLAST_FP64, ell_sel=None):

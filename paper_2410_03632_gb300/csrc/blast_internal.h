@@ -44,6 +44,7 @@ struct Workspace {
     DevBuf meta;    // per-request descriptors
     DevBuf tc;      // coefficient slices and scales of the tensor-core path
     DevBuf nl;      // non-linear spectra at the Limber points, staged from host requests
+    DevBuf ns;      // per-node Chebyshev coefficients (and staged samples) of non-separable spectra
     std::vector<char> hmeta;
 };
 
@@ -142,6 +143,11 @@ int launch_basis_slices(blast_plan *p, cudaStream_t s);
 // the request's non-linear table, mode 2 adds C^Limber(P_nl) - C^Limber(P_lin).
 int launch_limber(blast_plan *p, ReqDev *dreq, int nreq, const int *d_esel, int n_esel, int mode, int extended,
                   cudaStream_t s);
+// Non-separable spectra (nonsep.cu): per-node coefficients c[n][q] from the
+// samples Pq[q][j]; contraction and R sum into the separable FP64 path's partials.
+int launch_fit_nodes(blast_plan *p, const double *Pq, double *c, cudaStream_t s);
+int launch_contract_ns(blast_plan *p, const ReqDev *dreq, const double *c, const int *d_esel, int n_esel, double *Y,
+                       cudaStream_t s);
 bool tc_supported(const blast_plan *p);
 size_t tc_y_bytes(const blast_plan *p, int n, int n_esel);  // R-tile partials of a tensor-core call
 

@@ -618,6 +618,49 @@ extern "C" int blast_cl(blast_plan *p, const blast_request *req, int prec, doubl
     return blast_cl_batch(p, 1, req, prec, outs, out_mem_space, stream);
 }
 
+extern "C" int blast_cl_nonsep(blast_plan *p, const blast_request *req, const double *p_nodes, double *cl_out,
+                               int out_mem_space, void *stream)
+{
+    if (!p || !req || !p_nodes || !cl_out) return BLAST_EINVAL;
+    if (out_mem_space != 0 && out_mem_space != 1) return BLAST_EINVAL;
+    int rc = validate_request(p, req);
+    if (rc) return rc;
+    if (reinterpret_cast<uintptr_t>(p_nodes) % 8) return BLAST_EINVAL;
+    if (!p->have64) return BLAST_ENOBASIS;
+    if (*p->h_err) {
+        *p->h_err = 0;
+        return BLAST_ETIMEOUT;
+    }
+    BL_CUDA(cudaSetDevice(p->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    ReqDev *dreq = nullptr;
+    int *d_esel = nullptr, n_esel = 0;
+    std::vector<ReqDev> hreq;
+    std::vector<char> direct_out;
+    double *outs[1] = {cl_out};
+    if ((rc = stage_batch(p, 1, req, BLAST_FP64, outs, out_mem_space, s, &dreq, &d_esel, &n_esel, hreq, direct_out)))
+        return rc;
+    const size_t qn = (size_t)p->Q * p->N;
+    if ((rc = p->ws.ns.ensure(2 * qn * sizeof(double)))) return rc;
+    double *coef = p->ws.ns.as<double>();
+    const double *Pq = p_nodes;
+    if (req->mem_space == 0) {  // host samples: staged behind the coefficients
+        BL_CUDA(cudaMemcpyAsync(coef + qn, p_nodes, qn * sizeof(double), cudaMemcpyHostToDevice, s));
+        Pq = coef + qn;
+    }
+    if ((rc = prof_launch(p, BLAST_K_FIT, s, [&] { return launch_fit_nodes(p, Pq, coef, s); }))) return rc;
+    if ((rc = p->ws.ypart.ensure((size_t)3 * n_esel * p->X * p->max_tr * sizeof(double)))) return rc;
+    if ((rc = prof_launch(p, BLAST_K_CONTRACT, s, [&] {
+             return launch_contract_ns(p, dreq, coef, d_esel, n_esel, p->ws.ypart.as<double>(), s);
+         })))
+        return rc;
+    if ((rc = prof_launch(p, BLAST_K_REDUCE, s, [&] {
+             return launch_reduce(p, dreq, 1, BLAST_FP64, d_esel, n_esel, p->ws.ypart.p, s);
+         })))
+        return rc;
+    return finish_batch(p, 1, hreq, direct_out, outs, out_mem_space, s);
+}
+
 extern "C" int blast_test_trip_wait(blast_plan *p, int tile)
 {
     if (!p || tile < -1) return BLAST_EINVAL;

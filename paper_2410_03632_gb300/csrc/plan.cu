@@ -170,7 +170,7 @@ static void plan_free_device(blast_plan *p)
     if (p->h_err) cudaFreeHost(p->h_err);
     p->h_err = p->d_err = nullptr;
     p->ws.in.release(); p->ws.coef.release(); p->ws.wts.release();
-    p->ws.ypart.release(); p->ws.cl.release(); p->ws.meta.release(); p->ws.tc.release(); p->ws.nl.release();
+    p->ws.ypart.release(); p->ws.cl.release(); p->ws.meta.release(); p->ws.tc.release(); p->ws.nl.release(); p->ws.ns.release();
 }
 
 extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
