@@ -292,6 +292,14 @@ def run_blast(args):
 
     have_tc = bl.blast_cl_batch(plan.h, reqs[:2], bl.BLAST_BF16S, out_ptrs[:2], 1, stream.cuda_stream) == 0
     torch.cuda.synchronize()
+    tuned = None
+    if have_tc and not args.no_autotune:  # launch parameters picked on this batch (outside the timed region)
+        t0 = time.perf_counter()
+        rc = bl.blast_autotune(plan.h, reqs, args.tune_cache, stream.cuda_stream)
+        if rc == 0:
+            g_, w_, n_ = bl.blast_tuned_params(plan.h)
+            tuned = {"contract_ctas": g_, "reduce_warps": w_, "reduce_stages": n_,
+                     "seconds": time.perf_counter() - t0}
     prec_main = bl.BLAST_BF16S if have_tc else bl.BLAST_FP32
     dtype_main = "bf16 5-slice exact split (tcgen05)" if have_tc else "f32"
 
@@ -479,6 +487,7 @@ def run_blast(args):
                                "req_per_s": 1e3 * len(lat) / sum(lat),
                                "what": "one blast_cl call per cosmology, FP64 path, device inputs, back to back"},
         "roofline": roof,
+        "autotune": tuned,
         "kernel_bounds": kern,
         "alu_peaks": alu,
         "e2e": {"value": job_throughput(world, B, args.steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -571,6 +580,8 @@ def main():
                     help="offered request rate of the serving-latency run (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the serving-latency run (0 = skip)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch parameters")
+    ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read, then appended)")
     ap.add_argument("--basis-cache", default=None,
                     help="file to load the FP64 basis from (or save it to after computing it)")
     args = ap.parse_args()

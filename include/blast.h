@@ -342,6 +342,20 @@ int blast_profile_reset(blast_plan *plan);
  * context stays usable; -1 cancels.  Errors: BLAST_EINVAL. */
 int blast_test_trip_wait(blast_plan *plan, int tile);
 
+/* Autotuner of the BLAST_BF16S launch parameters: the contraction's number
+ * of persistent CTAs and the reduction's chi-chunk warps and stages per warp.
+ * The candidates run the caller's representative batch reqs[0..n) (device
+ * outputs the call allocates and frees) under the kernel timer; the fastest
+ * set stays in the plan for later calls of any batch size.  cache_path
+ * (optional) is a text file keyed by GPU name, plan dimensions and cosmology
+ * tiles: a key found there is used without timing; a new choice is appended.
+ * The tuned set never changes a result beyond the summation order of the
+ * chi sum.  Errors: BLAST_EINVAL (plan not served by the tensor cores),
+ * BLAST_ENOBASIS, BLAST_ENOMEM, and those of blast_cl_batch.
+ * blast_tuned_params reads the current set (0 = built-in choice). */
+int blast_autotune(blast_plan *plan, int n, const blast_request *reqs, const char *cache_path, void *stream);
+int blast_tuned_params(const blast_plan *plan, int *grid, int *red_warps, int *red_stages);
+
 /* Human-readable name of a status code (static string). */
 const char *blast_status_str(int status);
 

@@ -85,6 +85,8 @@ def lib():
             L.blast_cl_noalloc.argtypes = [P, ctypes.POINTER(blast_request), P, P]
             L.blast_set_coef_envelope.argtypes = [P, P]
             L.blast_limber_k.argtypes = [P, _dp]
+            L.blast_autotune.argtypes = [P, i, ctypes.POINTER(blast_request), ctypes.c_char_p, P]
+            L.blast_tuned_params.argtypes = [P, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
             L.blast_cl_nonsep.argtypes = [P, ctypes.POINTER(blast_request), P, P, i, P]
             L.blast_test_trip_wait.argtypes = [P, i]
             L.blast_cl_limber.argtypes = [P, ctypes.POINTER(blast_request), P, i, P, i, P]
@@ -155,6 +157,18 @@ def blast_test_trip_wait(h, tile):
 
 def blast_cl_nonsep(h, req, p_nodes_ptr, out_ptr, out_mem_space, stream=None):
     return lib().blast_cl_nonsep(h, ctypes.byref(req), p_nodes_ptr, out_ptr, out_mem_space, stream)
+
+
+def blast_autotune(h, reqs, cache_path=None, stream=None):
+    arr = (blast_request * len(reqs))(*reqs)
+    path = None if cache_path is None else str(cache_path).encode()
+    return lib().blast_autotune(h, len(reqs), arr, path, stream)
+
+
+def blast_tuned_params(h):
+    g, w, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().blast_tuned_params(h, ctypes.byref(g), ctypes.byref(w), ctypes.byref(n)), "blast_tuned_params")
+    return g.value, w.value, n.value
 
 
 def blast_limber_k(h, L, X):

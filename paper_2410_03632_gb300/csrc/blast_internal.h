@@ -83,6 +83,13 @@ struct blast_plan {
 
     Workspace ws;
 
+    // launch parameters of the tensor-core kernels (0 = built-in choice), set by blast_autotune
+    struct {
+        int grid = 0;            // persistent CTAs of the contraction
+        int red_w = 0, red_ns = 0;  // chi-chunk warps and stages per warp of the reduction
+        int nbt = 0;             // cosmology tiles of the batch size tuned for
+    } tune;
+
     // per-kernel-class launch counts and (optional) event timing
     bool prof_on = false;
     long long launches[BLAST_K_CLASSES] = {0};

@@ -1025,7 +1025,9 @@ int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const CUtensorM
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     const int units = args.nbt * args.ngr * args.nqt;
-    int grid = sms / args.nbt * args.nbt;
+    // persistent CTAs: the autotuned count when set, else every SM
+    int grid = p->tune.grid > 0 ? p->tune.grid : sms / args.nbt * args.nbt;
+    grid = grid / args.nbt * args.nbt;
     if (grid > units) grid = units;
     if (grid < args.nbt) grid = args.nbt;
     BL_CUDA(cudaFuncSetAttribute(k_contract_tc<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem));
@@ -1116,8 +1118,14 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
     const size_t stage = ((size_t)RT * kNB * 64 + 2 * MT * 32) * 4 + 8;
     // 8 warps (chi chunks), 4 for large stages, with as many stages each as fit
     // two blocks per SM
-    const int W = stage > 8192 ? 4 : 8;
+    // chi-chunk warps and stages: the autotuned pair when set (and fitting),
+    // else 8 warps (4 for large stages) with as many stages as fit two blocks per SM
+    int W = stage > 8192 ? 4 : 8;
     int NS = (int)((110 * 1024) / (W * stage));
+    if (p->tune.red_w > 0 && p->tune.red_ns > 0 && (size_t)p->tune.red_w * p->tune.red_ns * stage <= 220 * 1024) {
+        W = p->tune.red_w;
+        NS = p->tune.red_ns;
+    }
     if (NS > 4) NS = 4;
     if (NS < 1) return BLAST_EINVAL;
     const size_t smem = (size_t)W * NS * stage;
