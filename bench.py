@@ -469,6 +469,11 @@ def run_blast(args):
     if args.serve_seconds > 0 and rank == 0 and wl == "c1":
         serve = serve_latency(plan, rqs, prec_main, dtype_main, args.serve_rate, args.serve_seconds)
 
+    mixed = None
+    if args.serve_mix and rank == 0 and wl == "c1":
+        mixed = serve_mix(plan, rqs, prec_main, dtype_main, args.serve_rate, max(args.serve_seconds, 1.0),
+                          basis_cache=args.basis_cache_mix)
+
     launches = sum(prof_main[n][1] for n in bl.KERNEL_CLASS_NAMES)
     value = job_throughput(world, B, args.steps, ms_main * 1e-3)
     line = {
@@ -483,6 +488,7 @@ def run_blast(args):
                         "by_ell_type": {f"{l}:{'gg gs ss'.split()[t]}": v for (l, t), v in sorted(table.items())}
                         if wl != "c1" else None},
         "latency_ms": serve,
+        "serving_mix": mixed,
         "sequential_fp64_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                                "req_per_s": 1e3 * len(lat) / sum(lat),
                                "what": "one blast_cl call per cosmology, FP64 path, device inputs, back to back"},
@@ -506,34 +512,39 @@ def run_blast(args):
         dist.destroy_process_group()
 
 
-def serve_latency(plan, rqs, prec, prec_name, rate, seconds, seed=2000):
-    """Serving latency through blast_submit / blast_poll: seeded Poisson
-    arrivals at ``rate`` requests/s for ``seconds``, host inputs cycling over
-    ``rqs``; latency = submit call to the end of the poll that returns the C_l."""
+def serve_stream(srv, lanes, weights, rate, seconds, prec, seed=2000):
+    """Drive a server with seeded Poisson arrivals at ``rate`` requests/s for
+    ``seconds``: arrival i goes to lane l with probability weights[l] and takes
+    the lane's next request (cycling over lanes[l], a list of (blast_request,
+    output shape)); host inputs.  Latency = from the submit call to the end of
+    the poll that returns the C_l (a poller thread per lane, in submit order).
+    Returns p50/p99 overall and per lane."""
     import queue
     import threading
 
     from paper_2410_03632_gb300 import blast as bl
-    srv = bl.Server([plan], hbm_budget=32 << 30, max_slots=256)
-    reqs = [plan.request(rq) for rq in rqs]
-    P = bl.blast_npairs(rqs[0].n_clust, rqs[0].n_lens)
     n = max(1, int(rate * seconds))
-    gaps = np.random.default_rng(seed).exponential(1.0 / rate, n)
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, n)
+    w = np.asarray(weights, float)
+    pick = rng.choice(len(lanes), size=n, p=w / w.sum())
     sub_t, done_t, status = [0.0] * n, [0.0] * n, [0] * n
-    work = queue.Queue()
-    out = np.empty((P, plan.L))
+    qs = [queue.Queue() for _ in lanes]
+    outs = [np.empty(max(sh[0] * sh[1] for _, sh in ln)) for ln in lanes]
 
-    def poller():
+    def poller(li):
         while True:
-            item = work.get()
+            item = qs[li].get()
             if item is None:
                 return
             i, t = item
-            status[i], _ = bl.blast_poll(srv.h, t, out.ctypes.data, -1)
+            status[i], _ = bl.blast_poll(srv.h, t, outs[li].ctypes.data, -1)
             done_t[i] = time.perf_counter()
 
-    th = threading.Thread(target=poller)
-    th.start()
+    th = [threading.Thread(target=poller, args=(li,)) for li in range(len(lanes))]
+    for t in th:
+        t.start()
+    nxt_req = [0] * len(lanes)
     t0 = time.perf_counter()
     nxt, busy = t0, 0
     for i in range(n):
@@ -543,26 +554,126 @@ def serve_latency(plan, rqs, prec, prec_name, rate, seconds, seed=2000):
             if d <= 0:
                 break
             time.sleep(min(d, 5e-4))
+        li = int(pick[i])
+        r = lanes[li][nxt_req[li] % len(lanes[li])][0]
+        nxt_req[li] += 1
         sub_t[i] = time.perf_counter()
-        rc, t = bl.blast_submit(srv.h, 0, reqs[i % len(reqs)], prec)
+        rc, t = bl.blast_submit(srv.h, li, r, prec)
         while rc == bl.BLAST_EBUSY:  # admission pushed back: the wait counts as latency
             busy += 1
             time.sleep(1e-4)
-            rc, t = bl.blast_submit(srv.h, 0, reqs[i % len(reqs)], prec)
+            rc, t = bl.blast_submit(srv.h, li, r, prec)
         if rc != 0:
             raise RuntimeError(f"blast_submit: {bl.blast_status_str(rc)}")
-        work.put((i, t))
-    work.put(None)
-    th.join()
-    srv.close()
-    if any(status):
-        raise RuntimeError("blast_poll failed")
-    lat = sorted((b - a) * 1e3 for a, b in zip(sub_t, done_t))
+        qs[li].put((i, t))
+    for q in qs:
+        q.put(None)
+    for t in th:
+        t.join()
+    bad = [(int(pick[i]), bl.blast_status_str(status[i])) for i in range(n) if status[i]]
+    if bad:
+        from collections import Counter
+        raise RuntimeError(f"blast_poll failed for {len(bad)} of {n} requests: {dict(Counter(bad))}")
     wall = max(done_t) - t0
-    return {"p50": lat[n // 2], "p99": lat[min(n - 1, int(0.99 * n))], "max": lat[-1], "requests": n,
-            "offered_req_s": rate, "served_req_s": n / wall, "busy_retries": busy, "precision": prec_name,
-            "what": "server (blast_submit/blast_poll, continuous batching, max 256 per batch), seeded Poisson "
-                    "arrivals, host inputs; submit to completed poll"}
+
+    def pct(ix):
+        lat = sorted((done_t[i] - sub_t[i]) * 1e3 for i in ix)
+        if not lat:
+            return None
+        return {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "max": lat[-1],
+                "requests": len(lat)}
+
+    res = pct(range(n))
+    res.update({"offered_req_s": rate, "served_req_s": n / wall, "busy_retries": busy,
+                "lanes": [pct([i for i in range(n) if pick[i] == li]) for li in range(len(lanes))]})
+    return res
+
+
+def serve_latency(plan, rqs, prec, prec_name, rate, seconds, seed=2000):
+    """Serving latency of the 3x2pt grid alone through blast_submit / blast_poll."""
+    from paper_2410_03632_gb300 import blast as bl
+    srv = bl.Server([plan], hbm_budget=32 << 30, max_slots=256)
+    try:
+        lane = [(plan.request(rq), (bl.blast_npairs(rq.n_clust, rq.n_lens), plan.L)) for rq in rqs]
+        res = serve_stream(srv, [lane], [1.0], rate, seconds, prec, seed)
+    finally:
+        srv.close()
+    res.pop("lanes")
+    res.update({"precision": prec_name,
+                "what": "server (blast_submit/blast_poll, continuous batching, max 256 per batch), seeded Poisson "
+                        "arrivals, host inputs; submit to completed poll"})
+    return res
+
+
+def serve_mix(plan1, rqs1, prec, prec_name, rate, seconds, basis_cache=None, max_slots=256):
+    """Serving of a request stream that mixes the three workloads in size: a
+    third 5+5-bin requests on the 3x2pt grid, a third 10+10-bin requests and a
+    third ragged requests (own bin counts and ell sets) on the 10+10-bin order-96
+    grid; both plans resident, one server lane each.  Each lane's stream is also
+    served alone (same lane rate, the other lane idle) and every request kind is
+    timed one by one on the FP64 path, which the server's latencies are set
+    against."""
+    import torch
+
+    from paper_2410_03632_gb300 import blast as bl
+    from paper_2410_03632_gb300 import synth
+    t0 = time.perf_counter()
+    plan2 = bl.Plan(synth.plan_spec("c2"), device=plan1.device)
+    if basis_cache and os.path.exists(basis_cache):
+        bl.blast_basis_load(plan2.h, basis_cache, bl.BASIS_ALL)
+    else:
+        plan2.precompute(bl.BASIS_ALL)
+        if basis_cache:
+            bl.blast_basis_save(plan2.h, basis_cache)
+    basis_s = time.perf_counter() - t0
+    chi2, R2, _ = plan2.nodes()
+    L2 = plan2.L
+    kinds = {"c1": [], "c2": [], "c3": []}
+    for rq in rqs1[:16]:
+        kinds["c1"].append((plan1.request(rq), (bl.blast_npairs(rq.n_clust, rq.n_lens), plan1.L)))
+    for i in range(16):
+        rq = synth.config_request("c2", chi2, R2, 5000 + i)
+        kinds["c2"].append((plan2.request(rq), (bl.blast_npairs(rq.n_clust, rq.n_lens), L2)))
+        rq3, sel = synth.ragged_request(chi2, R2, 5000 + i, L2)
+        kinds["c3"].append((plan2.request(rq3, ell_sel=sel), (bl.blast_npairs(rq3.n_clust, rq3.n_lens), len(sel))))
+    lane2 = [x for pair in zip(kinds["c2"], kinds["c3"]) for x in pair]  # alternating 10+10 and ragged
+
+    # sequential FP64 comparator: one blast_cl per request, host inputs and outputs
+    seq = {}
+    for name, items in kinds.items():
+        pl = plan1 if name == "c1" else plan2
+        out = np.empty(max(sh[0] * sh[1] for _, sh in items))
+        lat = []
+        for k in range(3 + 24):
+            r, _ = items[k % len(items)]
+            a = time.perf_counter()
+            rc = bl.blast_cl(pl.h, r, bl.BLAST_FP64, out.ctypes.data, 0, None)
+            if rc != 0:
+                raise RuntimeError(bl.blast_status_str(rc))
+            if k >= 3:
+                lat.append((time.perf_counter() - a) * 1e3)
+        lat.sort()
+        seq[name] = {"p50": lat[len(lat) // 2], "p99": lat[-1], "req_per_s": 1e3 * len(lat) / sum(lat)}
+    torch.cuda.synchronize()
+
+    srv = bl.Server([plan1, plan2], hbm_budget=64 << 30, max_slots=max_slots)
+    try:
+        reserved = srv.reserved()
+        alone1 = serve_stream(srv, [kinds["c1"], lane2], [1.0, 0.0], rate / 3.0, seconds, prec, seed=2002)
+        alone2 = serve_stream(srv, [kinds["c1"], lane2], [0.0, 1.0], 2.0 * rate / 3.0, seconds, prec, seed=2003)
+        mix = serve_stream(srv, [kinds["c1"], lane2], [1.0, 2.0], rate, seconds, prec, seed=2001)
+    finally:
+        srv.close()
+        plan2.close()
+    return {"mix": mix, "alone": [alone1["lanes"][0], alone2["lanes"][1]],
+            "alone_served_req_s": [alone1["served_req_s"], alone2["served_req_s"]],
+            "sequential_fp64_ms": seq, "server_reserved_bytes": reserved, "precision": prec_name,
+            "basis_seconds_10x10_grid": basis_s, "max_slots": max_slots,
+            "what": ("two resident plans (3x2pt 5+5 grid; 10+10 order-96 grid), one server lane each; seeded Poisson "
+                     "arrivals, a third each 5+5, 10+10 and ragged requests; lane 0 = 5+5, lane 1 = 10+10 and "
+                     "ragged alternating; 'alone' = the lane's own stream with the other lane idle; latency from "
+                     "submit to completed poll, host inputs; sequential_fp64 = one blast_cl per request, host "
+                     "inputs and outputs")}
 
 
 def main():
@@ -580,8 +691,12 @@ def main():
                     help="offered request rate of the serving-latency run (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=2.0,
                     help="length of the serving-latency run (0 = skip)")
+    ap.add_argument("--serve-mix", action="store_true",
+                    help="also serve a stream mixing the 5+5, 10+10 and ragged workloads over two resident plans "
+                         "(computes the 10+10 grid's basis: minutes)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch parameters")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read, then appended)")
+    ap.add_argument("--basis-cache-mix", default=None, help="basis file of the 10+10 grid for --serve-mix")
     ap.add_argument("--basis-cache", default=None,
                     help="file to load the FP64 basis from (or save it to after computing it)")
     args = ap.parse_args()

@@ -278,8 +278,8 @@ int blast_set_coef_envelope(blast_plan *plan, const double *env);
 #define BLAST_NOALLOC_SCRATCH_BYTES (16u << 20)
 int blast_cl_noalloc(blast_plan *plan, const blast_request *req, double *cl_out, void *stream);
 
-/* Device bytes one request occupies while in flight (inputs, coefficients,
- * weights, partial sums, outputs); the server admits requests against it. */
+/* Device bytes one request occupies while in flight in blast_cl (inputs,
+ * coefficients, weights, partial sums, outputs): a sizing aid for callers. */
 size_t blast_request_footprint(const blast_plan *plan, const blast_request *req);
 
 /* ---------------------------------------------------------------- serving
@@ -288,20 +288,28 @@ size_t blast_request_footprint(const blast_plan *plan, const blast_request *req)
  * once and reused for every cosmology; requests share it).
  *
  * blast_server_create: plans[0..n_plans) stay owned by the caller, must outlive
- *   the server, and must not be used by other calls while it exists (its worker
- *   uses their work space).  hbm_budget bounds the summed
- *   blast_request_footprint of the requests admitted and not yet evaluated;
- *   max_slots bounds a batch.  One worker thread and one stream per plan.
+ *   the server, and must not be used by other calls while it exists (its
+ *   workers use their work space); a plan may appear once.  Each plan gets a
+ *   lane: a worker thread, a stream, the plan's work space reserved for
+ *   batches of max_slots requests, and a ring of 2 max_slots device slots, each
+ *   holding the inputs and the C_l of the largest request the plan accepts (one
+ *   batch running while the next forms).  All of it is allocated here; no
+ *   device memory is allocated afterwards.  hbm_budget bounds the device bytes
+ *   reserved in total (blast_server_reserved): BLAST_ENOMEM if they exceed it
+ *   or an allocation fails, BLAST_EINVAL for a repeated or null plan.
+ * blast_server_reserved: device bytes the server holds (0 for null).
  * blast_submit: copies the request's inputs (host or device, per mem_space)
  *   into server-owned pinned memory before it returns, checks them as
- *   blast_cl would (BLAST_EINVAL, BLAST_ENOBASIS), and admits the request:
- *   BLAST_EBUSY when the budget or the queue (16 max_slots) is full now (retry
- *   later), BLAST_ENOMEM when the request alone exceeds the budget.  *ticket
- *   identifies it.  The oldest waiting request fixes the (plan, precision) of
- *   the next batch; waiting requests with the same pair join it in arrival
- *   order, up to max_slots.  A request's C_l does not depend on its batch
- *   (FP64 bitwise equal to blast_cl).  A batch that fails is re-run request
- *   by request, so a bad request fails alone.
+ *   blast_cl would (BLAST_EINVAL, BLAST_ENOBASIS; n_ptab at most 1024), and
+ *   admits the request when its plan's ring has a free slot and the queue
+ *   (16 max_slots) has room, else BLAST_EBUSY (retry later; a slot frees when
+ *   its batch ends).  *ticket identifies it.  A lane's oldest waiting request
+ *   fixes the precision of the lane's next batch; its waiting requests with
+ *   that precision join in arrival order, up to max_slots.  Lanes run
+ *   concurrently.  A request's C_l does not depend on its batch or on the
+ *   other lanes (FP64 bitwise equal to blast_cl; BF16S bitwise equal to the
+ *   request evaluated alone).  A batch that fails is re-run request by
+ *   request, so a bad request fails alone.
  * blast_poll: waits up to timeout_us microseconds (negative = until done) for
  *   the ticket.  Not done: BLAST_ENOTREADY, *done = 0.  Done: *done = 1, the
  *   request's status is returned, on success C[npairs][n_sel] is copied to
@@ -315,6 +323,7 @@ int blast_server_create(blast_plan *const *plans, int n_plans, size_t hbm_budget
 int blast_submit(blast_server *server, int plan_idx, const blast_request *req, int precision, uint64_t *ticket);
 int blast_poll(blast_server *server, uint64_t ticket, double *cl_out, int *done, int64_t timeout_us);
 int blast_server_destroy(blast_server *server);
+size_t blast_server_reserved(const blast_server *server);
 
 /* Kernel classes of the evaluation path, for blast_profile_read. */
 #define BLAST_K_FIT 0         /* step (a0): Chebyshev fit */

@@ -98,6 +98,8 @@ def lib():
             L.blast_submit.argtypes = [P, i, ctypes.POINTER(blast_request), i, ctypes.POINTER(ctypes.c_uint64)]
             L.blast_poll.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(i), ctypes.c_int64]
             L.blast_server_destroy.argtypes = [P]
+            L.blast_server_reserved.argtypes = [P]
+            L.blast_server_reserved.restype = sz
             _LIB = L
     return _LIB
 
@@ -231,6 +233,11 @@ def blast_server_destroy(h):
     return lib().blast_server_destroy(h)
 
 
+def blast_server_reserved(h):
+    """Device bytes the server reserved at creation."""
+    return lib().blast_server_reserved(h)
+
+
 def blast_profile_enable(h, enable):
     _check(lib().blast_profile_enable(h, int(enable)), "blast_profile_enable")
 
@@ -276,6 +283,7 @@ class Plan:
 
     def __init__(self, spec, device: int = 0):
         self.spec = spec
+        self.device = device
         self._ell = np.ascontiguousarray(spec.ells, dtype=np.int32)
         d = blast_plan_desc()
         d.n_ell = self._ell.size
@@ -390,6 +398,9 @@ class Server:
         """(status, ticket) for a synth.Request; inputs are copied before it returns."""
         r = self.plans[plan_idx].request(rq, ell_sel)
         return blast_submit(self.h, plan_idx, r, precision)
+
+    def reserved(self):
+        return blast_server_reserved(self.h)
 
     def poll(self, ticket, shape, timeout_us=-1):
         """(status, C or None)."""

@@ -25,6 +25,19 @@
 
 void blast_last_error(const char *file, int line, const char *msg);
 
+// Lets `func` launch with up to the device's opt-in shared memory per block.
+// Every caller writes the same value, so plans served from several host
+// threads cannot race on the attribute (a per-launch size written by one
+// thread could fall under the size another thread launches with).
+template <class F>
+inline cudaError_t allow_opt_in_smem(F *func, int device)
+{
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
 // Device buffer owned by the library ------------------------------------------
 struct DevBuf {
     void *p = nullptr;
@@ -157,6 +170,11 @@ int launch_contract_ns(blast_plan *p, const ReqDev *dreq, const double *c, const
                        cudaStream_t s);
 bool tc_supported(const blast_plan *p);
 size_t tc_y_bytes(const blast_plan *p, int n, int n_esel);  // R-tile partials of a tensor-core call
+size_t tc_ws_total(const blast_plan *p, int n);  // coefficient slices, scales and chi weights of a call
+int tc_reserve(blast_plan *p, int n);
+// Work space for batches of up to nmax requests with device inputs and outputs,
+// every ell and any precision, allocated now; *bytes = the plan's work space.
+int plan_reserve(blast_plan *p, int nmax, size_t *bytes);
 
 // Host helpers
 int plan_alloc_basis(blast_plan *p, unsigned mask);

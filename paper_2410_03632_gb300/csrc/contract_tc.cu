@@ -959,15 +959,16 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 EncodeTiledFn encode_fn()
 {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    // looked up once; the initialisation of a function-local static is thread safe
+    static const EncodeTiledFn fn = [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
+            return (EncodeTiledFn)p;
+        return (EncodeTiledFn) nullptr;
+    }();
     return fn;
 }
 
@@ -1030,7 +1031,7 @@ int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const CUtensorM
     grid = grid / args.nbt * args.nbt;
     if (grid > units) grid = units;
     if (grid < args.nbt) grid = args.nbt;
-    BL_CUDA(cudaFuncSetAttribute(k_contract_tc<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::kSmem));
+    BL_CUDA(allow_opt_in_smem(k_contract_tc<KC>, p->device));
     k_contract_tc<KC><<<grid, kThreads, C::kSmem, s>>>(mapB, mapA4, args);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
@@ -1045,6 +1046,14 @@ bool tc_supported(const blast_plan *p)
 {
     return p->Kmma <= 96 && p->Rn % kQT == 0 && p->max_clust <= 2 * kNB && p->max_lens <= 2 * kNB;
 }
+
+size_t tc_ws_total(const blast_plan *p, int n)
+{
+    const int Bpad = bpad_of(n);
+    return tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad) + tc_u_bytes(p, Bpad);
+}
+
+int tc_reserve(blast_plan *p, int n) { return p->ws.tc.ensure(tc_ws_total(p, n)); }
 
 size_t tc_y_bytes(const blast_plan *p, int n, int n_esel)
 {
@@ -1131,11 +1140,11 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
     const size_t smem = (size_t)W * NS * stage;
     dim3 grid(Bpad / 32, n_esel, 3 * ngr);
     if (MT > kNB) {
-        BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<2 * kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BL_CUDA(allow_opt_in_smem(k_reduce_tc<2 * kNB>, p->device));
         k_reduce_tc<2 * kNB><<<grid, 32 * W, smem, s>>>(dreq, (const float *)ypart, U, n, p->X, p->L, d_esel,
                                                        n_esel, RT, MT, Bpad / 32, ngr, NS, p->d_pref, p->d_err);
     } else {
-        BL_CUDA(cudaFuncSetAttribute(k_reduce_tc<kNB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BL_CUDA(allow_opt_in_smem(k_reduce_tc<kNB>, p->device));
         k_reduce_tc<kNB><<<grid, 32 * W, smem, s>>>(dreq, (const float *)ypart, U, n, p->X, p->L, d_esel, n_esel,
                                                     RT, MT, Bpad / 32, ngr, NS, p->d_pref, p->d_err);
     }

@@ -9,6 +9,7 @@
 //        C^{AB}_ij(l)   = N_AB(l) sum_a U_i(a) Y^{AB}_l(a, j),
 //        U_i(a) = wchi_a chi_a D(chi_a) K^A_i(chi_a)              (Eq. final_cls)
 // with c_n(chi1, chi2) = D(chi1) D(chi2) a_n folded into U and V.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -265,7 +266,7 @@ int preload_fp64_kernels()
 int launch_fit(blast_plan *p, ReqDev *dreq, int nreq, cudaStream_t s)
 {
     size_t smem = sizeof(double) * (10 * kMaxPtab + p->N);
-    BL_CUDA(cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BL_CUDA(allow_opt_in_smem(k_fit, p->device));
     k_fit<<<nreq, kFitThreads, smem, s>>>(dreq, p->N, p->d_kcheb_u, p->d_cos_tab);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
@@ -511,6 +512,27 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
     if ((rc = prof_launch(p, BLAST_K_WEIGHTS, s, [&] { return launch_weights(p, dreq, n, prec != BLAST_FP64, s, prec == BLAST_FP64); }))) return rc;
     *dreq_out = dreq;
     *d_esel = de;
+    return BLAST_OK;
+}
+
+int plan_reserve(blast_plan *p, int nmax, size_t *bytes)
+{
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const int ntr_max = p->max_clust + p->max_lens;
+    const size_t coef_per = al((size_t)p->N * 8) + al((size_t)p->N * 4) + al((size_t)kMaxPtab * 8);
+    const size_t wts_per = al((size_t)ntr_max * p->X * 8) + al((size_t)ntr_max * p->Q * 8) +
+                           al((size_t)ntr_max * p->X * 4) + al((size_t)ntr_max * p->Q * 4);
+    size_t y = (size_t)nmax * 3 * p->L * p->X * p->max_tr * 8;  // CUDA-core partials (FP64)
+    if (tc_supported(p)) y = std::max(y, tc_y_bytes(p, nmax, p->L));
+    int rc;
+    BL_CUDA(cudaSetDevice(p->device));
+    if ((rc = p->ws.coef.ensure(coef_per * nmax)) || (rc = p->ws.wts.ensure(wts_per * nmax)) ||
+        (rc = p->ws.meta.ensure(sizeof(ReqDev) * nmax + sizeof(int) * BLAST_MAX_ELL)) ||
+        (rc = p->ws.ypart.ensure(y)) || (tc_supported(p) && (rc = tc_reserve(p, nmax))))
+        return rc;
+    if (bytes)
+        *bytes = p->ws.coef.bytes + p->ws.wts.bytes + p->ws.meta.bytes + p->ws.ypart.bytes + p->ws.tc.bytes +
+                 p->ws.in.bytes + p->ws.cl.bytes;
     return BLAST_OK;
 }
 

@@ -127,7 +127,7 @@ int launch_limber(blast_plan *p, ReqDev *dreq, int nreq, const int *d_esel, int 
     const int ntr = p->max_clust + p->max_lens;
     const size_t smem = sizeof(double) * ((size_t)p->X + (size_t)(extended ? 3 : 1) * ntr * p->X);
     if (smem > 220 * 1024) return BLAST_EINVAL;
-    BL_CUDA(cudaFuncSetAttribute(k_limber, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BL_CUDA(allow_opt_in_smem(k_limber, p->device));
     dim3 grid(n_esel, nreq);
     k_limber<<<grid, kLimThreads, smem, s>>>(dreq, p->d_chi, p->d_wchi, p->X, d_esel, p->d_ell, mode, extended);
     BL_CUDA(cudaGetLastError());

@@ -193,7 +193,7 @@ int launch_gemm_rows(blast_plan *p, const double *A, const double *kq, const int
                      cudaStream_t s)
 {
     size_t smem = sizeof(double) * ((size_t)kMC * 3 * p->N + (size_t)(1 + kRT) * kMC * kG + (size_t)kMC * kG * kRT);
-    BL_CUDA(cudaFuncSetAttribute(k_basis_gemm<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BL_CUDA(allow_opt_in_smem(k_basis_gemm<ROWS>, p->device));
     dim3 grid((p->Rn + kRT - 1) / kRT, p->X);
     for (int e0 = 0; e0 < p->L; e0 += kG) {
         k_basis_gemm<ROWS><<<grid, kThreads, smem, s>>>(A, kq, p->Nk, p->N, ell, p->L, e0, p->d_chi, R,

@@ -4,7 +4,9 @@ Bars: a request's C_l from the server equals the direct blast_cl result
 (bitwise for FP64; for BF16S bitwise equal to the same request evaluated
 alone), whatever else shares its batch; inputs are copied at submit (the
 caller's arrays may go away); admission, tickets and bounded polls follow the
-documented statuses.
+documented statuses; the reservation made at creation is checked against the
+budget; plans served at once from several threads give the results each
+request gets alone.
 """
 import numpy as np
 import pytest
@@ -38,6 +40,21 @@ def subset_request(full, ng, ns, max_clust):
 def plans():
     out = []
     for name in ("tiny", "tc"):
+        p = bl.Plan(synth.plan_spec(name))
+        p.precompute(bl.BASIS_ALL)
+        chi, R, _ = p.nodes()
+        out.append((name, p, chi, R))
+    yield out
+    for _, p, _, _ in out:
+        p.close()
+
+
+@pytest.fixture(scope="module")
+def more_tc():
+    """Tensor-core plans of other shapes: 7 + 6 tracers (two tracer groups) and
+    Chebyshev order 80 (two K chunks)."""
+    out = []
+    for name in ("tcg", "tck"):
         p = bl.Plan(synth.plan_spec(name))
         p.precompute(bl.BASIS_ALL)
         chi, R, _ = p.nodes()
@@ -109,20 +126,30 @@ def test_server_copies_device_inputs_at_submit(plans):
         srv.close()
 
 
+def test_server_reservation_and_budget(plans):
+    name, p, chi, R = plans[1]
+    srv = bl.Server([p], max_slots=3)
+    try:
+        need = srv.reserved()
+        # the ring (6 slots of the largest request) plus the plan's work space
+        assert need > 6 * 8 * (p.spec.max_clust + p.spec.max_lens) * p.X
+    finally:
+        srv.close()
+    with pytest.raises(bl.BlastError) as ei:
+        bl.Server([p], hbm_budget=need - 1, max_slots=3)
+    assert ei.value.status == bl.BLAST_ENOMEM
+    srv = bl.Server([p], hbm_budget=need, max_slots=3)
+    srv.close()
+    with pytest.raises(bl.BlastError) as ei:  # a plan's work space serves one lane
+        bl.Server([p, p], max_slots=3)
+    assert ei.value.status == bl.BLAST_EINVAL
+
+
 def test_server_admission_and_statuses(plans):
     name, p, chi, R = plans[1]
     spec = p.spec
     rq = synth.config_request(name, chi, R, 5)
-    fp = bl.blast_request_footprint(p.h, p.request(rq))
-    assert fp > 0
-
-    srv = bl.Server([p], hbm_budget=fp - 1, max_slots=4)
-    try:
-        assert srv.submit(0, rq, bl.BLAST_FP64)[0] == bl.BLAST_ENOMEM  # can never fit
-    finally:
-        srv.close()
-
-    srv = bl.Server([p], hbm_budget=2 * fp, max_slots=4)
+    srv = bl.Server([p], max_slots=2)  # a ring of four device slots
     try:
         bad = synth.Request(spec.max_clust + 1, 0, rq.kern_chi, rq.kern_Rchi, rq.growth_chi, rq.growth_Rchi,
                             rq.k_tab, rq.p_tab)
@@ -133,7 +160,7 @@ def test_server_admission_and_statuses(plans):
         assert short.k_tab[0] > p.nodes()[2].min()
         assert srv.submit(0, short, bl.BLAST_FP64)[0] == bl.BLAST_EINVAL
         assert srv.poll(123456789, (1, 1))[0] == bl.BLAST_EINVAL
-        # a burst far faster than the GPU: the two-request budget must push back
+        # a burst far faster than the GPU: the four slots must push back
         ok, busy = [], 0
         for _ in range(40):
             rc, t = srv.submit(0, rq, bl.BLAST_FP64)
@@ -151,6 +178,10 @@ def test_server_admission_and_statuses(plans):
             assert rc == bl.BLAST_OK
             ref = C if ref is None else ref
             assert np.array_equal(C, ref)
+        # slots are free again once their batches ended
+        rc, t = srv.submit(0, rq, bl.BLAST_FP64)
+        assert rc == bl.BLAST_OK
+        assert srv.poll(t, ref.shape, timeout_us=30_000_000)[0] == bl.BLAST_OK
         # BF16S on a plan the tensor-core kernel cannot serve
         tiny = plans[0][1]
         srv2 = bl.Server([tiny], max_slots=2)
@@ -163,11 +194,67 @@ def test_server_admission_and_statuses(plans):
         srv.close()
 
 
+def test_server_lanes_under_load_equal_alone(plans, more_tc):
+    """Three tensor-core plans of different shapes (tracer groups, Chebyshev
+    order) served at once from three submitting threads: every result equals
+    the same request evaluated alone, bit for bit."""
+    import threading
+    lanes = [plans[1]] + more_tc
+    work = []
+    for li, (name, p, chi, R) in enumerate(lanes):
+        rqs = [synth.config_request(name, chi, R, 300 + i) for i in range(6)]
+        jobs = [(rqs[i % 6], bl.BLAST_BF16S if i % 3 else bl.BLAST_FP64) for i in range(48)]
+        alone = {}
+        for i, (rq, prec) in enumerate(jobs[:12]):
+            alone[(i % 6, prec)] = p.cl(rq, prec)
+        work.append((jobs, alone))
+    srv = bl.Server([p for _, p, _, _ in lanes], max_slots=4)
+    errors = []
+
+    def client(li):
+        jobs, alone = work[li]
+        p = lanes[li][1]
+        try:
+            inflight = []
+            for i, (rq, prec) in enumerate(jobs):
+                while True:
+                    rc, t = srv.submit(li, rq, prec)
+                    if rc == bl.BLAST_OK:
+                        break
+                    assert rc == bl.BLAST_EBUSY
+                    if inflight:  # drain the oldest to free a slot
+                        j, tt = inflight.pop(0)
+                        _check(li, j, tt)
+                inflight.append((i, t))
+            for j, tt in inflight:
+                _check(li, j, tt)
+        except Exception as e:  # surfaced in the main thread
+            errors.append(e)
+
+    def _check(li, j, t):
+        jobs, alone = work[li]
+        rq, prec = jobs[j]
+        ref = alone[(j % 6, prec)]
+        rc, C = srv.poll(t, ref.shape, timeout_us=60_000_000)
+        assert rc == bl.BLAST_OK, bl.blast_status_str(rc)
+        assert np.array_equal(C, ref)
+
+    try:
+        th = [threading.Thread(target=client, args=(li,)) for li in range(len(lanes))]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+    finally:
+        srv.close()
+    assert not errors, errors[0]
+
+
 def test_server_destroy_evaluates_waiting_requests(plans):
     name, p, chi, R = plans[1]
     rq = synth.config_request(name, chi, R, 9)
     srv = bl.Server([p], max_slots=2)
-    for _ in range(6):
+    for _ in range(4):
         assert srv.submit(0, rq, bl.BLAST_FP64)[0] == bl.BLAST_OK
     srv.close()  # returns after the waiting requests ran; nothing leaks or hangs
     assert p.cl(rq, bl.BLAST_FP64).shape[1] == p.L  # the plan is usable again
