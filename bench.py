@@ -659,6 +659,7 @@ def serve_mix(plan1, rqs1, prec, prec_name, rate, seconds, basis_cache=None, max
     srv = bl.Server([plan1, plan2], hbm_budget=64 << 30, max_slots=max_slots)
     try:
         reserved = srv.reserved()
+        serve_stream(srv, [kinds["c1"], lane2], [1.0, 2.0], min(rate, 500.0), 0.5, prec, seed=1)  # warm-up
         alone1 = serve_stream(srv, [kinds["c1"], lane2], [1.0, 0.0], rate / 3.0, seconds, prec, seed=2002)
         alone2 = serve_stream(srv, [kinds["c1"], lane2], [0.0, 1.0], 2.0 * rate / 3.0, seconds, prec, seed=2003)
         mix = serve_stream(srv, [kinds["c1"], lane2], [1.0, 2.0], rate, seconds, prec, seed=2001)

@@ -19,23 +19,27 @@
         cudaError_t _e = (expr);                                                  \
         if (_e != cudaSuccess) {                                                  \
             blast_last_error(__FILE__, __LINE__, cudaGetErrorString(_e));         \
+            cudaGetLastError(); /* a non-sticky error must not fail later calls */ \
             return BLAST_EDEVICE;                                                 \
         }                                                                         \
     } while (0)
 
 void blast_last_error(const char *file, int line, const char *msg);
 
-// Lets `func` launch with up to the device's opt-in shared memory per block.
-// Every caller writes the same value, so plans served from several host
-// threads cannot race on the attribute (a per-launch size written by one
-// thread could fall under the size another thread launches with).
+// Lets `func` launch with as much dynamic shared memory as the device allows a
+// block beside the kernel's static shared memory.  Every caller writes the same
+// value, so plans served from several host threads cannot race on the
+// attribute (a per-launch size written by one thread could fall under the size
+// another thread launches with).
 template <class F>
 inline cudaError_t allow_opt_in_smem(F *func, int device)
 {
     int optin = 0;
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, func)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
 }
 
 // Device buffer owned by the library ------------------------------------------

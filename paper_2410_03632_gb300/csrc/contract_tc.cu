@@ -55,7 +55,7 @@ constexpr int kQT = 32;                   // chi-R nodes per tile (MMA N)
 constexpr int kM = 128;                   // cosmologies per tile (MMA M)
 constexpr int kKC = 64;                   // K elements per 128-byte swizzle row (one TMA box)
 constexpr int kEP = 2;                    // epilogue warps per TMEM lane quadrant
-constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 8 epilogue warps
+constexpr int kThreads = 64 + 128 * kEP;  // 2 control warps + 4 kEP epilogue warps
 constexpr int kHC = kQT / kEP;            // columns per epilogue thread
 constexpr int kCS = 4;                    // columns per TMEM load step
 constexpr int kNB = 5;                    // tracers per weight group
@@ -79,7 +79,7 @@ template <int KC> struct TcCfg {
     static constexpr uint32_t kACol = kNBUF * LV * kQT;     // TMEM column of the coefficient slices
     static constexpr int kSliceTmem = KC == 1 ? kS : kS - 1;  // coefficient slices held in TMEM
     static constexpr uint32_t kA4Bytes = KC == 1 ? 0 : KC * kM * 128;  // slice 4: [chunk][128 rows][128 B]
-    static constexpr int kYbufFloats = 2 * 4 * kNB * 64;    // [parity][quadrant][tracer][hi, lo][lane]
+    static constexpr int kYbufFloats = 2 * 4 * (kEP - 1) * kNB * 64;  // [parity][quadrant][part-1][tracer][hi, lo][lane]
     static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + kA4Bytes + kCtrlBytes + kEselBytes +
                                     kYbufFloats * 4;
 };
@@ -472,7 +472,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
     uint32_t *tmem_slot = (uint32_t *)(never + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     int *s_esel = (int *)((unsigned char *)bars + kCtrlBytes);         // selected ells
-    float *ybuf = (float *)((unsigned char *)s_esel + kEselBytes);     // [2][4][NGB][2][32] column-half hand-over
+    float *ybuf = (float *)((unsigned char *)s_esel + kEselBytes);     // [2][4][kEP-1][NGB][2][32] column-part hand-over
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int btile = blockIdx.x % args.nbt;
@@ -619,6 +619,9 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
         const int bl_ = quad * 32 + lane;
         const int b = btile * kM + bl_;
         const bool valid = b < args.n;
+        // a quadrant whose 32 lanes are all padding (a batch smaller than the
+        // tile) only keeps the buffer hand-off in step
+        const bool qlive = btile * kM + quad * 32 < args.n;
         const ReqDev *rq = valid ? &args.reqs[b] : nullptr;
         const int ng = valid ? rq->n_clust : 0, ns = valid ? rq->n_lens : 0;
         const float sa = args.sa[b];
@@ -699,7 +702,8 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
                     float Sh[NGB], Sl[NGB];
 #pragma unroll
                     for (int j = 0; j < NGB; j++) { Sh[j] = 0.f; Sl[j] = 0.f; }
-                    if (!dead) {
+                    if (!dead && !qlive) mbar_arrive(&tempty[buf]);  // nothing of this buffer is read
+                    if (!dead && qlive) {
                         tc_fence_after();
                         const uint32_t tcol = tmem + lane_addr + buf * (LV * kQT) + cb;
                         // R-sum of this thread's columns, two columns per packed lane pair, as
@@ -769,20 +773,25 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
                             Sl[j] = -__fadd_rn(el, __fadd_rn(B2.x, B2.y));
                         }
                     }
-                    // the column halves meet: part 1 hands its pairs to part 0 through
+                    // the column parts meet: parts 1.. hand their pairs to part 0 through
                     // shared memory, double buffered by iteration
-                    float *yq = ybuf + ((size_t)(g & 1) * 4 + quad) * (NGB * 64);
-                    if (part == 1) {
+                    float *yq = ybuf + ((size_t)(g & 1) * 4 + quad) * ((kEP - 1) * NGB * 64);
+                    if (part > 0) {
+                        float *yp = yq + (part - 1) * (NGB * 64);
 #pragma unroll
-                        for (int j = 0; j < NGB; j++) { yq[j * 64 + lane] = Sh[j]; yq[j * 64 + 32 + lane] = Sl[j]; }
+                        for (int j = 0; j < NGB; j++) { yp[j * 64 + lane] = Sh[j]; yp[j * 64 + 32 + lane] = Sl[j]; }
                     }
                     named_bar_sync(bar_id, 32 * kEP);
                     if (part == 0 && !dead) {
 #pragma unroll
-                        for (int j = 0; j < NGB; j++) {
-                            float se;
-                            two_sum(Sh[j], yq[j * 64 + lane], Sh[j], se);
-                            Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, yq[j * 64 + 32 + lane]));
+                        for (int q = 0; q < kEP - 1; q++) {
+                            const float *yp = yq + q * (NGB * 64);
+#pragma unroll
+                            for (int j = 0; j < NGB; j++) {
+                                float se;
+                                two_sum(Sh[j], yp[j * 64 + lane], Sh[j], se);
+                                Sl[j] = __fadd_rn(Sl[j], __fadd_rn(se, yp[j * 64 + 32 + lane]));
+                            }
                         }
                         if (valid) {
                             // times the tile's scale (exact); the pair (hi, lo) of tracer j at
@@ -1125,8 +1134,6 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
         reinterpret_cast<const float *>(p->ws.tc.as<char>() + tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad));
     const int RT = p->Rn / kQT, MT = p->max_tr, ngr = (MT + kNB - 1) / kNB;
     const size_t stage = ((size_t)RT * kNB * 64 + 2 * MT * 32) * 4 + 8;
-    // 8 warps (chi chunks), 4 for large stages, with as many stages each as fit
-    // two blocks per SM
     // chi-chunk warps and stages: the autotuned pair when set (and fitting),
     // else 8 warps (4 for large stages) with as many stages as fit two blocks per SM
     int W = stage > 8192 ? 4 : 8;
@@ -1138,7 +1145,7 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
     if (NS > 4) NS = 4;
     if (NS < 1) return BLAST_EINVAL;
     const size_t smem = (size_t)W * NS * stage;
-    dim3 grid(Bpad / 32, n_esel, 3 * ngr);
+    dim3 grid((n + 31) / 32, n_esel, 3 * ngr);  // cosmology tiles of 32 that hold a request
     if (MT > kNB) {
         BL_CUDA(allow_opt_in_smem(k_reduce_tc<2 * kNB>, p->device));
         k_reduce_tc<2 * kNB><<<grid, 32 * W, smem, s>>>(dreq, (const float *)ypart, U, n, p->X, p->L, d_esel,

@@ -84,6 +84,21 @@ def test_tc_two_ragged_cosmology_tiles(tc_case):
     assert np.array_equal(outs[0], outs[125]) and np.array_equal(outs[4], outs[129])
 
 
+@pytest.mark.parametrize("n", [1, 31, 33, 64, 97])
+def test_tc_partial_tiles_equal_full_batch(tc_case, n):
+    """Batches that fill only some 32-lane quadrants of a tile (whose epilogue
+    warps skip the padding) give every cosmology the bits it gets in a full
+    tile of 128."""
+    spec, g, T, plan = tc_case
+    base = [synth.config_request("tc", g.chi, g.R, i) for i in range(7)]
+    full = plan.cl_batch([base[i % 7] for i in range(128)], bl.BLAST_BF16S)
+    part = plan.cl_batch([base[i % 7] for i in range(n)], bl.BLAST_BF16S)
+    for i in range(n):
+        assert np.array_equal(part[i], full[i])
+    C64 = plan.cl(base[(n - 1) % 7], bl.BLAST_FP64)
+    assert np.max(eij(part[n - 1], C64, spec.max_clust, spec.max_lens)) < TOL
+
+
 @pytest.mark.parametrize("name", ["tcg", "tck"])
 def test_tc_other_kernel_shapes(name):
     """The instances with tracer weights in two groups of five (7 + 6 tracers,
