@@ -265,6 +265,9 @@ def run_blast(args):
     dev = torch.device("cuda", local)
     wl = args.workload
     spec = synth.plan_spec("c1" if wl == "c1" else "c2")
+    if args.n_ell:  # the same grid on fewer ells: a smaller case for profiler captures
+        import dataclasses
+        spec = dataclasses.replace(spec, ells=synth.ell_list(args.n_ell, 2, int(spec.ells[-1])))
     plan = bl.Plan(spec, device=local)
     cache = args.basis_cache
     if cache and os.path.exists(cache):
@@ -480,7 +483,7 @@ def run_blast(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_main / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_main, "data": "synthetic",
-        "config": workload_config(B, world, wl),
+        "config": dict(workload_config(B, world, wl), **({"n_ell_override": args.n_ell} if args.n_ell else {})),
         "fp64": {"value": job_throughput(world, B, k64, ms_64 * 1e-3), "unit": UNIT, "ms_per_step": ms_64 / k64,
                  "dtype": "f64"},
         "err_vs_fp64": {"max_eij": err, "bound": 1e-4,
@@ -695,6 +698,8 @@ def main():
     ap.add_argument("--serve-mix", action="store_true",
                     help="also serve a stream mixing the 5+5, 10+10 and ragged workloads over two resident plans "
                          "(computes the 10+10 grid's basis: minutes)")
+    ap.add_argument("--n-ell", type=int, default=0,
+                    help="evaluate the workload's grid on this many log-spaced ells instead (profiler captures)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch parameters")
     ap.add_argument("--tune-cache", default=None, help="autotuner cache file (read, then appended)")
     ap.add_argument("--basis-cache-mix", default=None, help="basis file of the 10+10 grid for --serve-mix")
