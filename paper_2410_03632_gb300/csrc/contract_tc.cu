@@ -18,10 +18,10 @@
 // k, D_k 2^(-8k) = sum_{p+q=k} sum_n (A_p 2^-8p)(T_q 2^-8q), is a multiple of
 // 2^(-8k) below 2^(24-8k) in magnitude for K <= 96, so the FP32 tensor-core
 // accumulation of levels 0, 1 and 2 is exact.  The 15 slice pairs p+q <= 4
-// feed LV accumulators in TMEM: five levels when K <= 64, else four, the last
-// holding levels 3 and 4 together (their sum lies 2^-24 below the leading
-// level; its FP32 rounding, about 2^-23 of that sum per MMA, is far below the
-// 2^-40 truncation of the slices).  The epilogue combines the levels with two
+// feed five level accumulators in TMEM (two buffers of 5 x 32 columns).  For
+// K <= 64 all five coefficient slices sit in TMEM beside them; for K <= 96
+// (two 64-wide K chunks) slices 0..3 do and slice 4, used by one slice pair
+// per K step, is read from shared memory.  The epilogue combines the levels with two
 // exact fast two-sums and one plain sum of the small parts,
 //   W 2^-32 = m + lo,   m = fl(fl(D_0 + D_1) + D_2),   lo = (e_1 + e_2) + (D_3 + D_4),
 // and scales by 2^(ea + eT - 16).  The R sum that follows also cancels (w
@@ -35,10 +35,12 @@
 // slices resident in TMEM, B = basis slices in shared memory) into two
 // accumulator buffers, warps 2..9 run the epilogue (one TMEM lane = one
 // cosmology per thread, two warps per lane quadrant with 16 columns each,
-// quadrature weights of up to five tracers per kind in registers, five more
-// in shared memory, the two column halves joined by a named barrier).  Every
-// mbarrier wait is bounded; on timeout the kernel records an error code in
-// host-mapped memory and exits after its copies and MMAs in flight complete.
+// quadrature weights of the unit's five B-side tracers in registers, the two
+// column halves joined through shared memory at a named barrier).  A work unit
+// is (cosmology tile of 128, group of five B-side tracers, 32-node q tile);
+// plans with up to ten tracers per kind run two groups as separate units.
+// Every mbarrier wait is bounded; on timeout the kernel records an error code
+// in host-mapped memory and exits after its copies and MMAs in flight complete.
 #include <cuda.h>
 #include <cuda_bf16.h>
 

@@ -11,7 +11,8 @@ column T (|T_n| < 1) into slices A_p 2^-8p, T_q 2^-8q with integer A_p, T_q,
    two-sums has exact error terms (m + e1 + e2 = D'_0 + D'_1 + D'_2), and
    lo = fl(fl(e1 + e2) + fl(D'_3 + D'_4)) leaves W' = m + lo within 2^-21 of
    the exact sum W = sum_k D'_k;
-3. for order > 64 the kernel keeps levels 3 and 4 in one FP32 accumulator;
+3. levels 3 and 4 could share one FP32 accumulator (the kernel keeps all five
+   levels apart, for both orders <= 64 and <= 96, so this is margin only):
    with one rounding per K = 16 MMA step the merged level stays within 2^-17
    of D'_3 + D'_4, far below the slices' truncation (next item);
 4. the five levels hold sum_n a_n T_n to about 2^-40 per term of the scale
