@@ -50,6 +50,7 @@ def lib():
             i, d = ctypes.c_int, ctypes.c_double
             L.orc_chi_grid.argtypes = [i, d, d, _dp, _dp]
             L.orc_R_grid.argtypes = [i, d, d, _dp, _dp]
+            L.orc_R_grid_sym.argtypes = [i, _dp, _dp]
             L.orc_cc_grid.argtypes = [i, d, d, _dp, _dp, _dp, i]
             L.orc_cheb_knodes.argtypes = [i, d, d, i, _dp, _dp]
             L.orc_jl.argtypes = [i, d, _dp]
@@ -61,7 +62,7 @@ def lib():
             L.orc_prefactor.restype = d
             L.orc_npairs.argtypes = [i, i]
             L.orc_cl.argtypes = [i, _ip, i, i, _dp, _dp, _dp, _dp, i, _dp, _dp, i, i,
-                                 _dp, _dp, _dp, _dp, _dp, i]
+                                 _dp, _dp, _dp, _dp, _dp, i, i]
             L.orc_limber.argtypes = [i, _ip, i, _dp, _dp, i, i, _dp, _dp, _dp, i, _dp]
             L.orc_cl_nonsep.argtypes = [i, _ip, i, i, _dp, _dp, _dp, i, _dp, _dp, i, i, _dp, _dp, _dp]
             L.orc_limber_plin.argtypes = [i, _ip, i, _dp, _dp, i, _dp, _dp, _dp]
@@ -94,6 +95,13 @@ def chi_grid(X, lo, hi):
 def R_grid(Rn, lo, hi):
     R, w = np.empty(Rn), np.empty(Rn)
     _check(lib().orc_R_grid(Rn, lo, hi, _d(R)[1], _d(w)[1]), "R_grid")
+    return R, w
+
+
+def R_grid_sym(Rn):
+    """R nodes and weights on (0, 1] of the symmetrised form (App. A)."""
+    R, w = np.empty(Rn), np.empty(Rn)
+    _check(lib().orc_R_grid_sym(Rn, _d(R)[1], _d(w)[1]), "R_grid_sym")
     return R, w
 
 
@@ -162,9 +170,10 @@ def npairs(ng, ns):
 
 
 # --------------------------------------------------------------------------- C_l
-def cl(ells, chi, wchi, R, wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, nthreads=0):
+def cl(ells, chi, wchi, R, wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, nthreads=0, sym=False):
     """C[p][e] from T~[3][n_ell][N][X*Rn] and the fitted a_n (steps 5-6);
-    nthreads 0 = every OpenMP thread (independent (type, ell) items)."""
+    nthreads 0 = every OpenMP thread (independent (type, ell) items); sym: the
+    symmetrised form of App. A (R in (0, 1], both kernel orders)."""
     ells, pe = _i(ells)
     chi, pc = _d(chi)
     wchi, pwc = _d(wchi)
@@ -181,7 +190,7 @@ def cl(ells, chi, wchi, R, wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, nthreads=
     assert T.shape == (3, ells.size, N, X * Rn), T.shape
     C = np.empty((npairs(ng, ns), ells.size))
     _check(lib().orc_cl(ells.size, pe, X, Rn, pc, pwc, pR, pwR, N, pT, pa, ng, ns,
-                        pkc, pkR, pDc, pDR, _d(C)[1], int(nthreads)), "cl")
+                        pkc, pkR, pDc, pDR, _d(C)[1], int(nthreads), int(bool(sym))), "cl")
     return C
 
 
@@ -236,12 +245,15 @@ def cl_nonsep(ells, chi, wchi, wR, T, Pq, ng, ns, kchi, kRchi):
 class Grid:
     """The oracle's own grids for one plan description (all FP64)."""
 
-    def __init__(self, ells, X, chi_min, chi_max, Rn, R_min, R_max, N, k_min, k_max, Nk, k_map=0):
+    def __init__(self, ells, X, chi_min, chi_max, Rn, R_min, R_max, N, k_min, k_max, Nk, k_map=0, r_form=0):
+        """r_form 0: R in [R_min, R_max] (two panels meeting at R = 1); 1: the
+        symmetrised form on (0, 1] (App. A; R_min, R_max unused)."""
         self.ells = np.asarray(ells, dtype=np.int32)
         self.X, self.Rn, self.N, self.Nk, self.k_map = X, Rn, N, Nk, k_map
         self.k_min, self.k_max = k_min, k_max
+        self.r_form = int(r_form)
         self.chi, self.wchi = chi_grid(X, chi_min, chi_max)
-        self.R, self.wR = R_grid(Rn, R_min, R_max)
+        self.R, self.wR = R_grid_sym(Rn) if self.r_form else R_grid(Rn, R_min, R_max)
         self.chi1 = np.repeat(self.chi, Rn)                 # q = a*Rn + r
         self.chi2 = (self.chi[:, None] * self.R[None, :]).ravel()
 
@@ -254,6 +266,8 @@ class Grid:
         return fit(self.N, self.k_min, self.k_max, ktab, ptab, self.k_map)
 
     def cl_nonsep(self, T, Pq, ng, ns, kchi, kRchi, ell_subset=None):
+        if self.r_form:
+            raise NotImplementedError("the non-separable oracle uses the R in [R_min, R_max] form")
         ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
         return cl_nonsep(ells, self.chi, self.wchi, self.wR, T, Pq, ng, ns, kchi, kRchi)
 
@@ -268,4 +282,4 @@ class Grid:
     def cl(self, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, ell_subset=None, nthreads=0):
         ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
         return cl(ells, self.chi, self.wchi, self.R, self.wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi,
-                  nthreads)
+                  nthreads, sym=self.r_form == 1)

@@ -104,6 +104,26 @@ int orc_R_grid(int Rn, double lo, double hi, double *R, double *w)
     return 0;
 }
 
+/* R nodes of the symmetrised form (App. A, Eq. app1 and the integral after it:
+ * R in (0, 1]): the strictly positive points of the M = 2 Rn + 1 first-kind
+ * Chebyshev points on [-1, 1] (the middle one is 0), Rn of them, with the
+ * Fejer-1 weights of the M-point rule.  For f on [0, 1] extended evenly,
+ * int_0^1 f = (1/2) int_{-1}^{1} f(|x|) dx = sum_{x_k > 0} w_k f(x_k)
+ * + (1/2) w_mid f(0); f(0) = 0 here (j_l(0) = 0 for l >= 1), so the middle
+ * point is dropped.  Output ordered by increasing R. */
+int orc_R_grid_sym(int Rn, double *R, double *w)
+{
+    if (Rn < 1) return -1;
+    int M = 2 * Rn + 1;
+    double *x = (double *)malloc(sizeof(double) * M), *wx = (double *)malloc(sizeof(double) * M);
+    if (!x || !wx) { free(x); free(wx); return -2; }
+    orc_fejer1(M, x, wx);
+    /* increasing x: indices Rn + 1 .. 2 Rn are the positive points */
+    for (int i = 0; i < Rn; i++) { R[i] = x[Rn + 1 + i]; w[i] = wx[Rn + 1 + i]; }
+    free(x); free(wx);
+    return 0;
+}
+
 /* Clenshaw-Curtis rule with Nk = n+1 points (n even) on [kmin, kmax] (Sec. 3.2,
  * App. C): x_m = cos(m pi / n), k_m = (kmin+kmax)/2 + (kmax-kmin)/2 x_m, and
  * w_m = (c_m/n) [1 - sum_{j=1}^{n/2} b_j cos(2 j m pi / n) / (4 j^2 - 1)] times
@@ -419,10 +439,14 @@ int orc_npairs(int ng, int ns)
 /* ones already divided by chi^2), growth Dchi[a], DRchi[q].                 */
 /* Output C[p][e] in the pair order of orc_npairs.                          */
 /* ------------------------------------------------------------------------- */
+/* sym != 0: the symmetrised form (App. A), R in (0, 1]:                   */
+/*   C = N_AB sum_a sum_r wchi_a wR_r chi_a                                  */
+/*       [K^A_i(chi_a) K^B_j(R_r chi_a) + K^B_j(chi_a) K^A_i(R_r chi_a)] w    */
+/* (the kernels at chi_a are the rows of kchi, at R_r chi_a those of kRchi). */
 int orc_cl(int n_ell, const int *ell, int X, int Rn, const double *chi, const double *wchi,
            const double *R, const double *wR, int N, const double *T, const double *a,
            int ng, int ns, const double *kchi, const double *kRchi,
-           const double *Dchi, const double *DRchi, double *C, int nthreads)
+           const double *Dchi, const double *DRchi, double *C, int nthreads, int sym)
 {
     (void)R;
     if (n_ell < 1 || X < 1 || Rn < 1 || N < 1 || ng < 0 || ns < 0 || ng + ns < 1) return -1;
@@ -457,14 +481,25 @@ int orc_cl(int n_ell, const int *ell, int X, int Rn, const double *chi, const do
                 for (int j = (t == 1 ? 0 : i); j < nB; j++) {
                     const double *Ki = kchi + (size_t)(offA + i) * X;
                     const double *Kj = kRchi + (size_t)(offB + j) * Q;
+                    const double *Kj1 = kchi + (size_t)(offB + j) * X;  /* sym: B at chi */
+                    const double *Ki2 = kRchi + (size_t)(offA + i) * Q; /* sym: A at R chi */
                     double s = 0.0;
                     for (int aa = 0; aa < X; aa++) {
-                        double sr = 0.0;
-                        for (int r = 0; r < Rn; r++) {
-                            int q = aa * Rn + r;
-                            sr += wR[r] * Kj[q] * w[q];
+                        if (!sym) {
+                            double sr = 0.0;
+                            for (int r = 0; r < Rn; r++) {
+                                int q = aa * Rn + r;
+                                sr += wR[r] * Kj[q] * w[q];
+                            }
+                            s += wchi[aa] * chi[aa] * Ki[aa] * sr;
+                        } else {
+                            double sr = 0.0;
+                            for (int r = 0; r < Rn; r++) {
+                                int q = aa * Rn + r;
+                                sr += wR[r] * (Ki[aa] * Kj[q] + Kj1[aa] * Ki2[q]) * w[q];
+                            }
+                            s += wchi[aa] * chi[aa] * sr;
                         }
-                        s += wchi[aa] * chi[aa] * Ki[aa] * sr;
                     }
                     C[(size_t)p * n_ell + e] = pref * s;
                     p++;
