@@ -82,13 +82,22 @@ typedef enum {
  *   ell      n_ell integer multipoles, 2 <= ell, strictly increasing, n_ell <= 128
  *   chi      n_chi evenly spaced nodes on [chi_min, chi_max], composite Simpson
  *            weights (3/8 rule on the last three intervals when n_chi is even)
- *   R        n_R nodes, two panels [R_min, 1] and [1, R_max] of n_R/2 first-kind
- *            Chebyshev points each with Fejer-1 weights (n_R even, R_min < 1 < R_max)
+ *   R        r_form 0 (the split form, chi2 = R chi1 with R in [R_min, R_max]):
+ *            n_R nodes, two panels [R_min, 1] and [1, R_max] of n_R/2 first-kind
+ *            Chebyshev points each with Fejer-1 weights (n_R even, R_min < 1 < R_max);
+ *            r_form 1 (the symmetrised form of App. A, Eq. app1: R in (0, 1] and
+ *            C_ij = N_AB sum wchi wR chi [K^A_i(chi) K^B_j(R chi) + K^B_j(chi) K^A_i(R chi)] w):
+ *            the n_R positive points of the (2 n_R + 1)-point first-kind Chebyshev
+ *            rule on [-1, 1] with its Fejer-1 weights (the even extension of the R
+ *            integrand; the middle node R = 0 carries j_l(0) = 0); R_min and R_max
+ *            are ignored.  Plans of r_form 1 serve BLAST_FP64 and BLAST_FP32
+ *            (BLAST_BF16S, blast_cl_nonsep: BLAST_EINVAL)
  *   k        n_cheb Chebyshev coefficients over [k_min, k_max]; k_map 0 maps k
  *            linearly onto [-1, 1], k_map 1 maps ln k linearly
  *   n_kquad  Clenshaw-Curtis points of the basis k integral, 2^m + 1
  *   max_clust, max_lens  largest tracer counts a request may carry
- *   device   CUDA device ordinal that holds the plan's tables               */
+ *   device   CUDA device ordinal that holds the plan's tables
+ *   r_form   0 or 1, see R                                                   */
 typedef struct {
     int n_ell;
     const int32_t *ell;
@@ -102,6 +111,7 @@ typedef struct {
     int n_kquad;
     int max_clust, max_lens;
     int device;
+    int r_form;
 } blast_plan_desc;
 
 /* One cosmology.  Tracers 0..n_clust-1 are clustering, n_clust..n_clust+n_lens-1

@@ -35,7 +35,8 @@ class blast_plan_desc(ctypes.Structure):
                 ("n_R", ctypes.c_int), ("R_min", ctypes.c_double), ("R_max", ctypes.c_double),
                 ("n_cheb", ctypes.c_int), ("k_min", ctypes.c_double), ("k_max", ctypes.c_double),
                 ("k_map", ctypes.c_int), ("n_kquad", ctypes.c_int),
-                ("max_clust", ctypes.c_int), ("max_lens", ctypes.c_int), ("device", ctypes.c_int)]
+                ("max_clust", ctypes.c_int), ("max_lens", ctypes.c_int), ("device", ctypes.c_int),
+                ("r_form", ctypes.c_int)]
 
 
 class blast_request(ctypes.Structure):
@@ -292,6 +293,7 @@ class Plan:
         d.n_R, d.R_min, d.R_max = spec.n_R, spec.R_min, spec.R_max
         d.n_cheb, d.k_min, d.k_max, d.k_map = spec.n_cheb, spec.k_min, spec.k_max, spec.k_map
         d.n_kquad, d.max_clust, d.max_lens, d.device = spec.n_kquad, spec.max_clust, spec.max_lens, device
+        d.r_form = int(getattr(spec, "r_form", 0))
         self.h = blast_plan_create(d)
         self.L, self.X, self.Rn, self.N = d.n_ell, d.n_chi, d.n_R, d.n_cheb
         self.Q = self.X * self.Rn

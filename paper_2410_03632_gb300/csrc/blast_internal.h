@@ -69,6 +69,7 @@ struct blast_plan {
     // description (ells copied)
     std::vector<int32_t> ell;
     int L = 0, X = 0, Rn = 0, Q = 0, N = 0, Nk = 0, kmap = 0;
+    int r_form = 0;  // 0: R in [R_min, R_max]; 1: symmetrised form on (0, 1]
     double chi_min = 0, chi_max = 0, R_min = 0, R_max = 0, k_min = 0, k_max = 0;
     int max_clust = 0, max_lens = 0, max_tr = 0, device = 0;
 

@@ -1052,10 +1052,12 @@ int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const CUtensorM
 
 // Tensor-core path limits: Chebyshev order <= 96 (coefficient slices and two
 // accumulator buffers fit the 512 TMEM columns), n_R a multiple of 32 (whole
-// R-tiles), at most 10 tracers of each kind (two groups of five).
+// R-tiles), at most 10 tracers of each kind (two groups of five), the split R
+// form (the symmetrised form's gs term needs the weights of both kinds per unit).
 bool tc_supported(const blast_plan *p)
 {
-    return p->Kmma <= 96 && p->Rn % kQT == 0 && p->max_clust <= 2 * kNB && p->max_lens <= 2 * kNB;
+    return p->r_form == 0 && p->Kmma <= 96 && p->Rn % kQT == 0 && p->max_clust <= 2 * kNB &&
+           p->max_lens <= 2 * kNB;
 }
 
 size_t tc_ws_total(const blast_plan *p, int n)

@@ -178,11 +178,14 @@ template <> struct Prec<double> { static __device__ const double *a(const ReqDev
 template <> struct Prec<float> { static __device__ const float *a(const ReqDev &r) { return r.a32; }
                                  static __device__ const float *V(const ReqDev &r) { return r.V32; } };
 
-template <class T>
+// SYM (the symmetrised form of App. A): the gs list holds both kinds, so that
+// the reduction can add K^B_j(chi) sum_r V^A_i w to K^A_i(chi) sum_r V^B_j w.
+template <class T, bool SYM>
 __global__ void __launch_bounds__(128)
 k_contract(const ReqDev *__restrict__ reqs, const T *__restrict__ basis, int L, int N, int X, int Rn,
            const int *__restrict__ esel, int n_esel, int MT, T *__restrict__ Y)
 {
+    constexpr int MJ = SYM ? BLAST_MAX_TRACERS : BLAST_MAX_TRACERS / 2;  // tracers of one list
     extern __shared__ unsigned char smraw[];
     T *as = reinterpret_cast<T *>(smraw);  // [N]
     __shared__ T red[4][BLAST_MAX_TRACERS];
@@ -191,26 +194,26 @@ k_contract(const ReqDev *__restrict__ reqs, const T *__restrict__ basis, int L, 
     const int e = esel[es];
     const ReqDev &rq = reqs[b];
     const int ng = rq.n_clust, ns = rq.n_lens;
-    const int nB = (t == 0) ? ng : ns, offB = (t == 0) ? 0 : ng;
+    const int nB = (t == 0) ? ng : (SYM && t == 1) ? ng + ns : ns, offB = (t == 0 || (SYM && t == 1)) ? 0 : ng;
     const T *acoef = Prec<T>::a(rq);
     for (int n = threadIdx.x; n < N; n += blockDim.x) as[n] = acoef[n];
     __syncthreads();
     const int Q = X * Rn;
     const T *Tb = basis + ((size_t)t * L + e) * N * Q + (size_t)a * Rn;
     const T *V = Prec<T>::V(rq) + (size_t)offB * Q + (size_t)a * Rn;
-    T part[BLAST_MAX_TRACERS / 2];
+    T part[MJ];
 #pragma unroll
-    for (int j = 0; j < BLAST_MAX_TRACERS / 2; j++) part[j] = 0;
+    for (int j = 0; j < MJ; j++) part[j] = 0;
     for (int r = threadIdx.x; r < Rn; r += blockDim.x) {
         T w = 0;
         for (int n = 0; n < N; n++) w = fma(as[n], Tb[(size_t)n * Q + r], w);
 #pragma unroll
-        for (int j = 0; j < BLAST_MAX_TRACERS / 2; j++)
+        for (int j = 0; j < MJ; j++)
             if (j < nB) part[j] = fma(V[(size_t)j * Q + r], w, part[j]);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int j = 0; j < BLAST_MAX_TRACERS / 2; j++) {
+    for (int j = 0; j < MJ; j++) {
         if (j >= nB) break;
         T v = part[j];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -228,9 +231,12 @@ k_contract(const ReqDev *__restrict__ reqs, const T *__restrict__ basis, int L, 
 // Second half of (b): C_ij(l) = N_AB(l) sum_a U_i(a) Y[t][es][a][j], summed in
 // FP64, scattered to the request's output columns.
 // ---------------------------------------------------------------------------
+// sym: C_ij also gets N_AB(l) sum_a U_j(a) Y[t][es][a][i] (both kernel orders
+// of the symmetrised form, App. A); list positions are tracer rows minus the
+// list's first row.
 template <class T>
 __global__ void k_reduce(const ReqDev *__restrict__ reqs, const T *__restrict__ Y, int X, int L,
-                         const int *__restrict__ esel, int n_esel, int MT, const double *__restrict__ pref)
+                         const int *__restrict__ esel, int n_esel, int MT, const double *__restrict__ pref, int sym)
 {
     const int b = blockIdx.y;
     const ReqDev &rq = reqs[b];
@@ -242,9 +248,16 @@ __global__ void k_reduce(const ReqDev *__restrict__ reqs, const T *__restrict__ 
         int t, ia, jb, jloc;
         pair_decode(p, ng, ns, t, ia, jb, jloc);
         const double *U = rq.U64 + (size_t)ia * X;
-        const T *Yp = Y + (((size_t)b * 3 + t) * n_esel + es) * (size_t)X * MT + jloc;
+        const int first = (t == 0 || (sym && t == 1)) ? 0 : ng;  // first tracer row of the type's list
+        const T *Yb = Y + (((size_t)b * 3 + t) * n_esel + es) * (size_t)X * MT;
+        const T *Yp = Yb + (jb - first);
         double s = 0.0;
         for (int a = 0; a < X; a++) s = fma(U[a], (double)Yp[(size_t)a * MT], s);
+        if (sym) {
+            const double *Uj = rq.U64 + (size_t)jb * X;
+            const T *Yi = Yb + (ia - first);
+            for (int a = 0; a < X; a++) s = fma(Uj[a], (double)Yi[(size_t)a * MT], s);
+        }
         double out = pref[t * L + e] * s;
         if (rq.status) out = nan("");
         rq.cl[(size_t)p * rq.n_sel + col] = out;
@@ -258,7 +271,8 @@ int preload_fp64_kernels()
     cudaFuncAttributes fa;
     BL_CUDA(cudaFuncGetAttributes(&fa, k_fit));
     BL_CUDA(cudaFuncGetAttributes(&fa, k_weights));
-    BL_CUDA(cudaFuncGetAttributes(&fa, k_contract<double>));
+    BL_CUDA(cudaFuncGetAttributes(&fa, k_contract<double, false>));
+    BL_CUDA(cudaFuncGetAttributes(&fa, k_contract<double, true>));
     BL_CUDA(cudaFuncGetAttributes(&fa, k_reduce<double>));
     return BLAST_OK;
 }
@@ -284,12 +298,21 @@ int launch_contract(blast_plan *p, ReqDev *dreq, int nreq, int prec, const int *
                     void *ypart, cudaStream_t s)
 {
     dim3 grid(nreq, p->X, 3 * n_esel);
+    const size_t sm64 = sizeof(double) * p->N, sm32 = sizeof(float) * p->N;
     if (prec == BLAST_FP64) {
-        k_contract<double><<<grid, 128, sizeof(double) * p->N, s>>>(dreq, p->T64, p->L, p->N, p->X, p->Rn, d_esel,
-                                                                    n_esel, p->max_tr, (double *)ypart);
+        if (p->r_form == 1)
+            k_contract<double, true><<<grid, 128, sm64, s>>>(dreq, p->T64, p->L, p->N, p->X, p->Rn, d_esel, n_esel,
+                                                             p->max_tr, (double *)ypart);
+        else
+            k_contract<double, false><<<grid, 128, sm64, s>>>(dreq, p->T64, p->L, p->N, p->X, p->Rn, d_esel, n_esel,
+                                                              p->max_tr, (double *)ypart);
     } else {
-        k_contract<float><<<grid, 128, sizeof(float) * p->N, s>>>(dreq, p->T32, p->L, p->N, p->X, p->Rn, d_esel,
-                                                                  n_esel, p->max_tr, (float *)ypart);
+        if (p->r_form == 1)
+            k_contract<float, true><<<grid, 128, sm32, s>>>(dreq, p->T32, p->L, p->N, p->X, p->Rn, d_esel, n_esel,
+                                                            p->max_tr, (float *)ypart);
+        else
+            k_contract<float, false><<<grid, 128, sm32, s>>>(dreq, p->T32, p->L, p->N, p->X, p->Rn, d_esel, n_esel,
+                                                             p->max_tr, (float *)ypart);
     }
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
@@ -302,10 +325,10 @@ int launch_reduce(blast_plan *p, ReqDev *dreq, int nreq, int prec, const int *d_
     dim3 grid((pmax * n_esel + 127) / 128, nreq);
     if (prec == BLAST_FP64)
         k_reduce<double><<<grid, 128, 0, s>>>(dreq, (const double *)ypart, p->X, p->L, d_esel, n_esel, p->max_tr,
-                                              p->d_pref);
+                                              p->d_pref, p->r_form);
     else
         k_reduce<float><<<grid, 128, 0, s>>>(dreq, (const float *)ypart, p->X, p->L, d_esel, n_esel, p->max_tr,
-                                             p->d_pref);
+                                             p->d_pref, p->r_form);
     BL_CUDA(cudaGetLastError());
     return BLAST_OK;
 }
@@ -645,6 +668,7 @@ extern "C" int blast_cl_nonsep(blast_plan *p, const blast_request *req, const do
 {
     if (!p || !req || !p_nodes || !cl_out) return BLAST_EINVAL;
     if (out_mem_space != 0 && out_mem_space != 1) return BLAST_EINVAL;
+    if (p->r_form != 0) return BLAST_EINVAL;  // per-node contraction of the split R form only
     int rc = validate_request(p, req);
     if (rc) return rc;
     if (reinterpret_cast<uintptr_t>(p_nodes) % 8) return BLAST_EINVAL;

@@ -183,8 +183,9 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
         if (e && d->ell[e] <= d->ell[e - 1]) return BLAST_EINVAL;
     }
     if (d->n_chi < 4 || !(d->chi_min > 0) || !(d->chi_max > d->chi_min)) return BLAST_EINVAL;
-    if (d->n_R < 2 || d->n_R % 2 || d->n_R > 512 || !(d->R_min > 0) || !(d->R_min < 1.0) || !(d->R_max > 1.0))
-        return BLAST_EINVAL;
+    if (d->r_form != 0 && d->r_form != 1) return BLAST_EINVAL;
+    if (d->n_R < 2 || d->n_R % 2 || d->n_R > 512) return BLAST_EINVAL;
+    if (d->r_form == 0 && (!(d->R_min > 0) || !(d->R_min < 1.0) || !(d->R_max > 1.0))) return BLAST_EINVAL;
     if (d->n_cheb < 2 || d->n_cheb > 128 || !(d->k_min > 0) || !(d->k_max > d->k_min)) return BLAST_EINVAL;
     if (d->k_map < 0 || d->k_map > 1) return BLAST_EINVAL;
     int nq = d->n_kquad - 1;
@@ -201,7 +202,11 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
     p->chi_min = d->chi_min; p->chi_max = d->chi_max; p->R_min = d->R_min; p->R_max = d->R_max;
     p->k_min = d->k_min; p->k_max = d->k_max;
     p->max_clust = d->max_clust; p->max_lens = d->max_lens;
+    p->r_form = d->r_form;
+    // tracers per (type) list of partial sums: the B-side kind, or both kinds
+    // for gs in the symmetrised form (K^A_i at R chi enters too)
     p->max_tr = d->max_clust > d->max_lens ? d->max_clust : d->max_lens;
+    if (p->r_form == 1) p->max_tr = d->max_clust + d->max_lens;
     p->device = d->device;
     p->Kmma = (p->N + 15) / 16 * 16;
     p->Kst = p->Kmma > 64 ? p->Kmma : 64;
@@ -223,13 +228,26 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
         for (int i = 0; i < 4; i++) p->wchi[X - 4 + i] += c38[i] * 3.0 * h / 8.0;
     }
 
-    // R: two Fejer-1 panels meeting at R = 1
     std::vector<double> fx, fw;
-    fejer1(p->Rn / 2, fx, fw);
     p->R.resize(p->Rn);
     p->wR.resize(p->Rn);
     const int hn = p->Rn / 2;
-    for (int i = 0; i < hn; i++) {
+    if (p->r_form == 1) {
+        // R in (0, 1] (App. A): the positive points of the (2 n_R + 1)-point
+        // first-kind rule on [-1, 1], with its Fejer-1 weights: the even
+        // extension of the R integrand, whose value at R = 0 (the middle node)
+        // vanishes with j_l(0)
+        fejer1(2 * p->Rn + 1, fx, fw);
+        for (int i = 0; i < p->Rn; i++) {
+            p->R[i] = fx[p->Rn + 1 + i];
+            p->wR[i] = fw[p->Rn + 1 + i];
+        }
+        p->R_min = p->R[0];
+        p->R_max = 1.0;
+    }
+    // R: two Fejer-1 panels meeting at R = 1
+    if (p->r_form == 0) fejer1(p->Rn / 2, fx, fw);
+    for (int i = 0; i < hn && p->r_form == 0; i++) {
         double h1 = 0.5 * (1.0 - p->R_min), h2 = 0.5 * (p->R_max - 1.0);
         p->R[i] = 0.5 * (p->R_min + 1.0) + h1 * fx[i];
         p->wR[i] = h1 * fw[i];
@@ -257,7 +275,7 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
     // grid hash (for basis files)
     uint64_t hsh = fnv1a(p->ell.data(), sizeof(int32_t) * p->L);
     double dv[6] = {p->chi_min, p->chi_max, p->R_min, p->R_max, p->k_min, p->k_max};
-    int iv[5] = {p->X, p->Rn, p->N, p->Nk, p->kmap};
+    int iv[6] = {p->X, p->Rn, p->N, p->Nk, p->kmap, p->r_form};
     hsh = fnv1a(dv, sizeof dv, hsh);
     p->grid_hash = fnv1a(iv, sizeof iv, hsh);
 

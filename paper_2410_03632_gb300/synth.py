@@ -147,6 +147,7 @@ class PlanSpec:
     n_kquad: int
     max_clust: int
     max_lens: int
+    r_form: int = 0  # 0: R in [R_min, R_max]; 1: the symmetrised form on (0, 1]
 
 
 def kquad_points(k_min, k_max, chi_max, R_max):
