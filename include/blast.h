@@ -90,8 +90,8 @@ typedef enum {
  *            the n_R positive points of the (2 n_R + 1)-point first-kind Chebyshev
  *            rule on [-1, 1] with its Fejer-1 weights (the even extension of the R
  *            integrand; the middle node R = 0 carries j_l(0) = 0); R_min and R_max
- *            are ignored.  Plans of r_form 1 serve BLAST_FP64 and BLAST_FP32
- *            (BLAST_BF16S, blast_cl_nonsep: BLAST_EINVAL)
+ *            are ignored.  Plans of r_form 1 serve every precision;
+ *            blast_cl_nonsep refuses them (BLAST_EINVAL)
  *   k        n_cheb Chebyshev coefficients over [k_min, k_max]; k_map 0 maps k
  *            linearly onto [-1, 1], k_map 1 maps ln k linearly
  *   n_kquad  Clenshaw-Curtis points of the basis k integral, 2^m + 1

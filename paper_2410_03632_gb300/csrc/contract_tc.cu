@@ -435,14 +435,30 @@ __global__ void k_basis_slices(const double *__restrict__ T, int L, int N, int Q
 struct TcArgs {
     const ReqDev *reqs;
     int n, Bpad, nbt, ngr, nqt, n_esel, L, Q, Rn, RT, MT, X, Kst, Kmma;
+    int npass, sym;      // passes per q tile (3, or 4 for the symmetrised form)
     const int *esel;
     const float *scT;    // [3][L][Q / kQT] one scale per tile
     const float *sa;     // [Bpad]
     const uint16_t *A;   // [S][Bpad][Kst] coefficient slices
-    float *Y;            // [3][n_esel][X][Bpad/32][ngr][RT][5][hi, lo][32] R-tile partial pairs
+    float *Y;            // [npass][n_esel][X][Bpad/32][ngr][RT][5][hi, lo][32] R-tile partial pairs
     int *err;            // host-mapped error word
     int trip;            // test hook: tile at which CTA 0 waits on a barrier nothing completes (-1 off)
 };
+
+// Passes over one q tile: (basis type, kind of the B-side weights, 0 clustering
+// 1 lensing).  Split R form: gg (g), gs (s), ss (s).  Symmetrised form (App.
+// A, both kernel orders): gg (g), gs with the clustering weights (g) for the
+// K^s(chi) K^g(R chi) term, gs (s), ss (s).
+__host__ __device__ __forceinline__ int pass_basis(int pass, int sym)
+{
+    return sym ? (pass == 0 ? 0 : (pass == 3 ? 2 : 1)) : pass;
+}
+__host__ __device__ __forceinline__ int pass_kind(int pass, int sym) { return sym ? (pass >= 2) : (pass >= 1); }
+// kind of the A-side weights U of a pass
+__host__ __device__ __forceinline__ int pass_kind_a(int pass, int sym)
+{
+    return sym ? (pass == 1 || pass == 3) : (pass == 2);
+}
 
 // Work units: (cosmology tile, group of five B-side tracers, 32-column q
 // tile).  A CTA keeps its cosmology tile (the grid is a multiple of nbt), so
@@ -478,7 +494,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int btile = blockIdx.x % args.nbt;
-    const int n_iter_unit = 3 * args.n_esel;
+    const int n_iter_unit = args.npass * args.n_esel;
     const int n_units = args.nbt * args.ngr * args.nqt;
 
     if (threadIdx.x == 0) {
@@ -527,7 +543,7 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
                     break;
                 }
                 if (elect_one()) {
-                    const int t = it / args.n_esel, e = s_esel[it % args.n_esel];
+                    const int t = pass_basis(it / args.n_esel, args.sym), e = s_esel[it % args.n_esel];
                     const int row = (t * args.L + e) * args.Q + q0;
                     mbar_expect_tx(&full[st], C::kStageBytes);
 #pragma unroll
@@ -658,11 +674,12 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
             int grp, q0;
             unit_decode(args, u, grp, q0);
             const int a = q0 / args.Rn, rt = (q0 % args.Rn) / kQT;
-            for (int t = 0; t < 3; t++) {
-                const int offB = (t == 0) ? 0 : ng, nB = (t == 0) ? ng : ns;
-                if (t < 2) {
-                    // weights of the B-side kind (clustering for gg, lensing for gs and
-                    // ss), tracers 5 grp .. 5 grp + 4 of it
+            for (int t = 0; t < args.npass; t++) {  // t: pass (the Y index)
+                const int kindB = pass_kind(t, args.sym);
+                const int offB = kindB ? ng : 0, nB = kindB ? ns : ng;
+                if (t == 0 || kindB != pass_kind(t - 1, args.sym)) {
+                    // weights of the pass's B-side kind (passes of one kind follow each
+                    // other), tracers 5 grp .. 5 grp + 4 of it
 #pragma unroll
                     for (int j = 0; j < kNB; j++) {
                         const int jj = kNB * grp + j;
@@ -683,7 +700,9 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
                     const uint32_t tph = (g / kNBUF) & 1;
                     // the tile's scale 2^(eG - 16), fetched while the MMA finishes
                     const float tsc =
-                        (part == 0) ? args.scT[((size_t)t * args.L + s_esel[es]) * (args.Q / kQT) + q0 / kQT] : 0.f;
+                        (part == 0) ? args.scT[((size_t)pass_basis(t, args.sym) * args.L + s_esel[es]) * (args.Q / kQT) +
+                                               q0 / kQT]
+                                    : 0.f;
                     if (!dead) {
                         bool lost = *abort_flag != 0;
                         // test hook: one warp of CTA 0 waits, with a 20M-cycle limit, on a
@@ -827,11 +846,15 @@ k_contract_tc(const __grid_constant__ CUtensorMap mapB, const __grid_constant__ 
 // one bulk copy brings the 32 cosmologies' R-tile pairs of the group at a chi
 // node (contiguous in Y), another their chi weights; the chunks meet in a
 // tree through the same shared memory at the end.
+//
+// Symmetrised form (sym != 0): the block's pass gives one kernel order, every
+// pair (i, j) of it, times N_AB(l), is written to S[b][pass][i][j][es], and
+// k_sym_combine adds the two orders of each spectrum.
 template <int MTA>
 __global__ void __launch_bounds__(256)
 k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const float *__restrict__ U, int n,
             int X, int L, const int *__restrict__ esel, int n_esel, int RT, int MT, int nbt32, int ngr, int NS,
-            const double *__restrict__ pref, int *err)
+            const double *__restrict__ pref, int *err, int sym, double *__restrict__ S)
 {
     extern __shared__ __align__(128) unsigned char red_smem[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
@@ -840,7 +863,8 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
     const int b = bt * 32 + lane;
     const ReqDev *rq = (b < n) ? &reqs[b] : nullptr;
     const int ng = rq ? rq->n_clust : 0, ns = rq ? rq->n_lens : 0;
-    const int nA = (t == 2) ? ns : ng, nB = (t == 0) ? ng : ns, kindA = (t == 2) ? 1 : 0;
+    const int kindA = pass_kind_a(t, sym), kindB = pass_kind(t, sym);  // t: pass
+    const int nA = kindA ? ns : ng, nB = kindB ? ns : ng;
     const int e = esel[es];
     const int col = rq ? rq->e_out[e] : -1;
     const int yfl = RT * kNB * 64, ufl = 2 * MT * 32, stf = yfl + ufl;  // floats per stage
@@ -944,7 +968,19 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
         __syncthreads();
     }
     if (w != 0 || !rq || col < 0) return;
-    const double pf = pref[t * L + e];
+    const double pf = pref[pass_basis(t, sym) * L + e];
+    if (sym) {
+#pragma unroll
+        for (int i = 0; i < MTA; i++) {
+#pragma unroll
+            for (int j = 0; j < kNB; j++) {
+                const int jb = kNB * grp + j;
+                if (i >= nA || jb >= nB) continue;
+                S[((((size_t)b * 4 + t) * MT + i) * MT + jb) * n_esel + es] = pf * ((double)Zh[i][j] + (double)Zl[i][j]);
+            }
+        }
+        return;
+    }
     const int ngg = ng * (ng + 1) / 2, ngs = ng * ns;
 #pragma unroll
     for (int i = 0; i < MTA; i++) {
@@ -960,6 +996,40 @@ k_reduce_tc(const ReqDev *__restrict__ reqs, const float *__restrict__ Y, const 
             if (rq->status) out = nan("");
             rq->cl[(size_t)p * rq->n_sel + col] = out;
         }
+    }
+}
+
+// The symmetrised form's two kernel orders of every spectrum (App. A):
+//   gg, ss: C_ij = S[pass][i][j] + S[pass][j][i]   (i <= j; the diagonal doubles)
+//   gs:     C_ij = S[gs][i][j] + S[gs with clustering weights][j][i]
+// one addition per output, so the result does not depend on the launch.
+__global__ void k_sym_combine(const ReqDev *__restrict__ reqs, const double *__restrict__ S, int MT,
+                              const int *__restrict__ esel, int n_esel)
+{
+    const int b = blockIdx.y;
+    const ReqDev &rq = reqs[b];
+    const int ng = rq.n_clust, ns = rq.n_lens;
+    const int ngg = ng * (ng + 1) / 2, ngs = ng * ns, P = ngg + ngs + ns * (ns + 1) / 2;
+    const double *Sb = S + (size_t)b * 4 * MT * MT * n_esel;
+    auto at = [&](int pass, int i, int j, int es) { return Sb[(((size_t)pass * MT + i) * MT + j) * n_esel + es]; };
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < P * n_esel; idx += gridDim.x * blockDim.x) {
+        const int p = idx / n_esel, es = idx % n_esel;
+        const int col = rq.e_out[esel[es]];
+        if (col < 0) continue;
+        double v;
+        if (p < ngg || p >= ngg + ngs) {  // gg or ss: (i, j), i <= j, of the pass's kind
+            const bool ss = p >= ngg;
+            const int m = ss ? ns : ng;
+            int i = 0, rem = ss ? p - ngg - ngs : p;
+            while (rem >= m - i) { rem -= m - i; i++; }
+            const int j = i + rem, pass = ss ? 3 : 0;
+            v = at(pass, i, j, es) + at(pass, j, i, es);
+        } else {
+            const int i = (p - ngg) / ns, j = (p - ngg) % ns;  // clustering i, lensing j
+            v = at(2, i, j, es) + at(1, j, i, es);
+        }
+        if (rq.status) v = nan("");
+        rq.cl[(size_t)p * rq.n_sel + col] = v;
     }
 }
 
@@ -1027,7 +1097,10 @@ int bpad_of(int n) { return (n + kM - 1) / kM * kM; }
 // Work space of one tensor-core call: coefficient slices, scales, chi weights U.
 size_t tc_a_bytes(const blast_plan *p, int Bpad) { return ((size_t)kS * Bpad * p->Kst * 2 + 255) / 256 * 256; }
 size_t tc_sa_bytes(int Bpad) { return ((size_t)Bpad * 4 + 255) / 256 * 256; }
-size_t tc_u_bytes(const blast_plan *p, int Bpad) { return (size_t)Bpad * p->X * 4 * p->max_tr * 4; }
+// tracers per kind on the tensor-core path (the U and Y tracer dimension)
+int tc_mt(const blast_plan *p) { return p->max_clust > p->max_lens ? p->max_clust : p->max_lens; }
+int tc_npass(const blast_plan *p) { return p->r_form == 1 ? 4 : 3; }
+size_t tc_u_bytes(const blast_plan *p, int Bpad) { return (size_t)Bpad * p->X * 4 * tc_mt(p) * 4; }
 
 template <int KC>
 int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const CUtensorMap &mapA4, const TcArgs &args,
@@ -1052,12 +1125,10 @@ int launch_contract_inst(blast_plan *p, const CUtensorMap &mapB, const CUtensorM
 
 // Tensor-core path limits: Chebyshev order <= 96 (coefficient slices and two
 // accumulator buffers fit the 512 TMEM columns), n_R a multiple of 32 (whole
-// R-tiles), at most 10 tracers of each kind (two groups of five), the split R
-// form (the symmetrised form's gs term needs the weights of both kinds per unit).
+// R-tiles), at most 10 tracers of each kind (two groups of five).
 bool tc_supported(const blast_plan *p)
 {
-    return p->r_form == 0 && p->Kmma <= 96 && p->Rn % kQT == 0 && p->max_clust <= 2 * kNB &&
-           p->max_lens <= 2 * kNB;
+    return p->Kmma <= 96 && p->Rn % kQT == 0 && p->max_clust <= 2 * kNB && p->max_lens <= 2 * kNB;
 }
 
 size_t tc_ws_total(const blast_plan *p, int n)
@@ -1068,10 +1139,18 @@ size_t tc_ws_total(const blast_plan *p, int n)
 
 int tc_reserve(blast_plan *p, int n) { return p->ws.tc.ensure(tc_ws_total(p, n)); }
 
+// R-tile partials of every pass, then (symmetrised form) the per-order pair
+// sums S[b][pass][i][j][es] in FP64
+static size_t tc_y_only(const blast_plan *p, int n, int n_esel)
+{
+    const int ngr = (tc_mt(p) + kNB - 1) / kNB;
+    return ((size_t)tc_npass(p) * n_esel * p->X * bpad_of(n) * ngr * (p->Rn / kQT) * kNB * 2 * 4 + 255) / 256 * 256;
+}
+
 size_t tc_y_bytes(const blast_plan *p, int n, int n_esel)
 {
-    const int ngr = (p->max_tr + kNB - 1) / kNB;
-    return (size_t)3 * n_esel * p->X * bpad_of(n) * ngr * (p->Rn / kQT) * kNB * 2 * 4;
+    const size_t sym = p->r_form == 1 ? (size_t)bpad_of(n) * 4 * tc_mt(p) * tc_mt(p) * n_esel * 8 : 0;
+    return tc_y_only(p, n, n_esel) + sym;
 }
 
 int launch_basis_slices(blast_plan *p, cudaStream_t s)
@@ -1092,7 +1171,7 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     uint16_t *A = ws.tc.as<uint16_t>();
     float *sa = reinterpret_cast<float *>(ws.tc.as<char>() + tc_a_bytes(p, Bpad));
     float *U = reinterpret_cast<float *>(ws.tc.as<char>() + tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad));
-    k_coef_slices<<<Bpad / 8, 256, 0, s>>>(dreq, n, p->N, p->Kst, Bpad, A, sa, p->X, p->max_tr, U, p->d_env);
+    k_coef_slices<<<Bpad / 8, 256, 0, s>>>(dreq, n, p->N, p->Kst, Bpad, A, sa, p->X, tc_mt(p), U, p->d_env);
     BL_CUDA(cudaGetLastError());
 
     CUtensorMap mapB;
@@ -1108,7 +1187,9 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     args.Q = p->Q;
     args.Rn = p->Rn;
     args.RT = p->Rn / kQT;
-    args.MT = p->max_tr;
+    args.MT = tc_mt(p);
+    args.npass = tc_npass(p);
+    args.sym = p->r_form == 1;
     args.X = p->X;
     args.Kst = p->Kst;
     args.Kmma = p->Kmma;
@@ -1120,7 +1201,7 @@ int launch_contract_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, in
     args.err = p->d_err;
     args.trip = p->test_trip;
     p->test_trip = -1;  // one call only
-    args.ngr = (p->max_tr + kNB - 1) / kNB;
+    args.ngr = (tc_mt(p) + kNB - 1) / kNB;
     if (p->Kst > kKC) {
         // coefficient slice 4 for the shared-memory operand of the p = 4 MMAs
         CUtensorMap mapA4;
@@ -1136,7 +1217,9 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
     const int Bpad = bpad_of(n);
     const float *U =
         reinterpret_cast<const float *>(p->ws.tc.as<char>() + tc_a_bytes(p, Bpad) + tc_sa_bytes(Bpad));
-    const int RT = p->Rn / kQT, MT = p->max_tr, ngr = (MT + kNB - 1) / kNB;
+    const int RT = p->Rn / kQT, MT = tc_mt(p), ngr = (MT + kNB - 1) / kNB;
+    const int sym = p->r_form == 1, npass = tc_npass(p);
+    double *S = sym ? reinterpret_cast<double *>((char *)const_cast<void *>(ypart) + tc_y_only(p, n, n_esel)) : nullptr;
     const size_t stage = ((size_t)RT * kNB * 64 + 2 * MT * 32) * 4 + 8;
     // chi-chunk warps and stages: the autotuned pair when set (and fitting),
     // else 8 warps (4 for large stages) with as many stages as fit two blocks per SM
@@ -1149,16 +1232,22 @@ int launch_reduce_tc(blast_plan *p, ReqDev *dreq, int n, const int *d_esel, int 
     if (NS > 4) NS = 4;
     if (NS < 1) return BLAST_EINVAL;
     const size_t smem = (size_t)W * NS * stage;
-    dim3 grid((n + 31) / 32, n_esel, 3 * ngr);  // cosmology tiles of 32 that hold a request
+    dim3 grid((n + 31) / 32, n_esel, npass * ngr);  // cosmology tiles of 32 that hold a request
     if (MT > kNB) {
         BL_CUDA(allow_opt_in_smem(k_reduce_tc<2 * kNB>, p->device));
         k_reduce_tc<2 * kNB><<<grid, 32 * W, smem, s>>>(dreq, (const float *)ypart, U, n, p->X, p->L, d_esel,
-                                                       n_esel, RT, MT, Bpad / 32, ngr, NS, p->d_pref, p->d_err);
+                                                       n_esel, RT, MT, Bpad / 32, ngr, NS, p->d_pref, p->d_err, sym,
+                                                       S);
     } else {
         BL_CUDA(allow_opt_in_smem(k_reduce_tc<kNB>, p->device));
         k_reduce_tc<kNB><<<grid, 32 * W, smem, s>>>(dreq, (const float *)ypart, U, n, p->X, p->L, d_esel, n_esel,
-                                                    RT, MT, Bpad / 32, ngr, NS, p->d_pref, p->d_err);
+                                                    RT, MT, Bpad / 32, ngr, NS, p->d_pref, p->d_err, sym, S);
     }
     BL_CUDA(cudaGetLastError());
+    if (sym) {
+        const int pmax = blast_npairs(p->max_clust, p->max_lens);
+        k_sym_combine<<<dim3((pmax * n_esel + 127) / 128, n), 128, 0, s>>>(dreq, S, MT, d_esel, n_esel);
+        BL_CUDA(cudaGetLastError());
+    }
     return BLAST_OK;
 }

@@ -4,8 +4,10 @@ the C ABI against the oracle's symmetrised form.
 Bars as for the split form: R nodes equal the oracle's; basis within 1e-11 of
 its row maximum; FP64 C_l within e_ij <= 1e-10 and FP32 within 1e-4 of the
 oracle for uneven tracer counts and ell subsets; the allocation-free entry
-point gives blast_cl's FP64 bits; the tensor-core precision and the
-non-separable entry refuse such plans with BLAST_EINVAL.
+point gives blast_cl's FP64 bits; the non-separable entry refuses such plans
+with BLAST_EINVAL.  On tensor-core shapes (one and two tracer groups) the
+five-slice path is within e_ij <= 1e-4 of the oracle, and a cosmology's
+result is the same alone and in a batch.
 """
 import dataclasses
 
@@ -106,10 +108,32 @@ def test_noalloc_and_refusals(case):
     assert bl.blast_cl_noalloc(plan.h, r, out.data_ptr(), torch.cuda.current_stream().cuda_stream) == bl.BLAST_OK
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), ref)
-    with pytest.raises(bl.BlastError) as ei:
-        plan.cl(rq, bl.BLAST_BF16S)
-    assert ei.value.status == bl.BLAST_EINVAL
     Pq = np.ones((plan.Q, plan.N))
     with pytest.raises(bl.BlastError) as ei:
         plan.nonsep(rq, Pq)
     assert ei.value.status == bl.BLAST_EINVAL
+
+
+@pytest.mark.parametrize("name", ["tc", "tcg"])
+def test_tensor_core_symmetrised(name):
+    spec = dataclasses.replace(synth.plan_spec(name), r_form=1)
+    g = orc.Grid(spec.ells, spec.n_chi, spec.chi_min, spec.chi_max, spec.n_R, spec.R_min, spec.R_max,
+                 spec.n_cheb, spec.k_min, spec.k_max, spec.n_kquad, spec.k_map, r_form=1)
+    To = g.basis()
+    plan = bl.Plan(spec)
+    try:
+        plan.precompute(bl.BASIS_ALL)
+        L = spec.ells.size
+        counts = [(spec.max_clust, spec.max_lens), (1, 0), (0, 2), (2, 1), (spec.max_clust, 1)]
+        sels = [None, [0, L - 1], None, list(range(1, L, 2)), None]
+        rqs = [subset_request(synth.config_request(name, g.chi, g.R, 90 + i), min(ng, spec.max_clust),
+                              min(ns, spec.max_lens), spec.max_clust) for i, (ng, ns) in enumerate(counts)]
+        outs = plan.cl_batch(rqs, bl.BLAST_BF16S, sels)
+        for rq, sel, C in zip(rqs, sels, outs):
+            Co = _oracle(g, To, rq, sel)
+            assert np.max(eij(C, Co, rq.n_clust, rq.n_lens)) < TOL_FP32
+            C64 = plan.cl(rq, bl.BLAST_FP64, ell_sel=sel)
+            assert np.max(eij(C64, Co, rq.n_clust, rq.n_lens)) < TOL_FP64
+            assert np.array_equal(plan.cl(rq, bl.BLAST_BF16S, ell_sel=sel), C)
+    finally:
+        plan.close()
