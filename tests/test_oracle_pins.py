@@ -232,6 +232,37 @@ def test_basis_diagonal_matches_closed_form():
     assert abs(T[2, 0, 0, 0] - ref) <= 1.0 / (6 * kmax ** 3 * c * c) + 1e-10 * ref
 
 
+@pytest.mark.parametrize("kmap", [0, 1])
+def test_basis_all_types_and_both_maps_against_direct_quadrature(kmap):
+    """T~ of every type (gg f = k^2, gs f = 1, ss f = 1/k^2) and both k maps,
+    orders n < 6, against composite Gauss-Legendre in k with scipy's spherical
+    Bessel functions and numpy's Chebyshev polynomials: no Clenshaw-Curtis
+    rule, no recurrence, no map code of the oracle.  The panels are short
+    against the Bessel period; measured agreement is 1e-12 of the row or
+    better (the gg rows, weighted to high k, are the loosest)."""
+    kmin, kmax, N = 1e-3, 5.0, 6
+    pts = [(2, 300.0, 240.0), (9, 300.0, 300.0), (30, 410.0, 350.0)]
+    Nk = synth.kquad_points(kmin, kmax, 410.0, 1.0)
+    u, w = np.polynomial.legendre.leggauss(24)
+    edges = np.geomspace(kmin, kmax, 4001) if kmap else np.linspace(kmin, kmax, 4001)
+    lo, hi = edges[:-1, None], edges[1:, None]
+    kk = (0.5 * (hi - lo) * (u[None, :] + 1.0) + lo).ravel()
+    wk = (0.5 * (hi - lo) * w[None, :]).ravel()
+    if kmap:
+        x = 2.0 * (np.log(kk) - np.log(kmin)) / (np.log(kmax) - np.log(kmin)) - 1.0
+    else:
+        x = 2.0 * (kk - kmin) / (kmax - kmin) - 1.0
+    Tn = np.polynomial.chebyshev.chebvander(x, N - 1)  # [k][n]
+    f = [kk ** 2, np.ones_like(kk), kk ** -2.0]
+    for l, c1, c2 in pts:
+        T = orc.basis([l], [c1], [c2], N, kmin, kmax, Nk, kmap=kmap)
+        jj = sp.spherical_jn(l, kk * c1) * sp.spherical_jn(l, kk * c2)
+        for t in range(3):
+            ref = (wk * f[t] * jj) @ Tn
+            scale = np.max(np.abs(ref))
+            assert np.max(np.abs(T[t, 0, :, 0] - ref)) <= 5e-12 * scale, (kmap, l, t, T[t, 0, :, 0], ref)
+
+
 def test_basis_quadrature_converged_under_doubling():
     """The Clenshaw-Curtis size rule gives a converged T~ (App. C analog)."""
     spec = synth.plan_spec("tiny")
