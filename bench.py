@@ -149,41 +149,60 @@ def cpu_model():
 
 class OracleSample:
     """The FP64 oracle's per-cosmology evaluation (fit + contraction +
-    quadrature; the basis is excluded as in the paper) on the benchmark grid,
-    for a subset of ells.  The oracle's basis for this grid would take hours to
-    build on the host, and its evaluation loops cost the same whatever the
+    quadrature; the basis is excluded as in the paper) on a workload's grid,
+    for a subset of ells.  The oracle's basis for these grids would take hours
+    to build on the host, and its evaluation loops cost the same whatever the
     basis values are, so the sample feeds it a seeded random basis of the right
-    shape."""
+    shape.  c1: 4 cosmologies x every 4th of the 64 ells; c2: 2 cosmologies x
+    every 10th of the 100 ells; c3: 2 ragged requests (own bin counts), the
+    sample ells inside each request's own ell set, scaled by its size."""
 
-    def __init__(self, n_req=4, ell_stride=4, seed=7):
+    def __init__(self, n_req=None, workload="c1", seed=7):
         import oracle
         from paper_2410_03632_gb300 import synth
-        spec = synth.plan_spec("c1")
+        grid = "c1" if workload == "c1" else "c2"
+        spec = synth.plan_spec(grid)
+        stride = 4 if grid == "c1" else 10
+        n_req = n_req or (4 if grid == "c1" else 2)
         self.g = oracle.Grid(spec.ells, spec.n_chi, spec.chi_min, spec.chi_max, spec.n_R, spec.R_min,
                              spec.R_max, spec.n_cheb, spec.k_min, spec.k_max, spec.n_kquad, spec.k_map)
-        self.sub = spec.ells[::ell_stride]
+        sub_idx = np.arange(0, spec.ells.size, stride)
         rng = np.random.default_rng(seed)
-        self.T = rng.standard_normal((3, self.sub.size, spec.n_cheb, spec.n_chi * spec.n_R))
-        self.rqs = [synth.config_request("c1", self.g.chi, self.g.R, 1 + i) for i in range(n_req)]
-        self.sets = n_req * self.sub.size / spec.ells.size   # C_l-sets one run evaluates
-        self.desc = (f"{n_req} cosmologies x {self.sub.size} of {spec.ells.size} ells (every {ell_stride}th) "
-                     f"on the benchmark grid, oracle fit + contraction + quadrature, seeded random basis "
-                     f"of the right shape; scaled to full C_l-sets")
+        self.T = rng.standard_normal((3, sub_idx.size, spec.n_cheb, spec.n_chi * spec.n_R))
+        self.items = []  # (request, sample-ell positions, the C_l-set fraction it evaluates)
+        self._Tsel = {}
+        for i in range(n_req):
+            if workload == "c3":
+                rq, sel = synth.ragged_request(self.g.chi, self.g.R, 1 + i, spec.ells.size)
+                pos = [k for k, e in enumerate(sub_idx) if e in set(sel)]
+                self.items.append((rq, pos, len(pos) / len(sel)))
+                self._Tsel[i] = np.ascontiguousarray(self.T[:, pos])  # built here, not in the timed pass
+            else:
+                rq = synth.config_request(grid, self.g.chi, self.g.R, 1 + i)
+                self.items.append((rq, list(range(sub_idx.size)), sub_idx.size / spec.ells.size))
+        self.sub = spec.ells[sub_idx]
+        self.sets = sum(f for _, _, f in self.items)  # C_l-sets one run evaluates
+        self.desc = (f"{workload}: {n_req} cosmologies x every {stride}th of the {spec.ells.size} ells "
+                     f"(within each request's own ell set for c3) on the {grid} grid, oracle fit + contraction "
+                     f"+ quadrature, seeded random basis of the right shape; scaled to full C_l-sets")
 
     def run(self, threads):
         """Seconds for one pass over the sample with `threads` OpenMP threads."""
         t0 = time.perf_counter()
-        for rq in self.rqs:
+        for i, (rq, pos, _) in enumerate(self.items):
+            if not pos:
+                continue
             a = self.g.fit(rq.k_tab, rq.p_tab)
-            self.g.cl(self.T, a, rq.n_clust, rq.n_lens, rq.kern_chi, rq.kern_Rchi, rq.growth_chi,
-                      rq.growth_Rchi, ell_subset=self.sub, nthreads=threads)
+            T = self._Tsel.get(i, self.T)
+            self.g.cl(T, a, rq.n_clust, rq.n_lens, rq.kern_chi, rq.kern_Rchi,
+                      rq.growth_chi, rq.growth_Rchi, ell_subset=self.sub[pos], nthreads=threads)
         return time.perf_counter() - t0
 
 
-def cpu_baseline(reps=10):
+def cpu_baseline(reps=10, workload="c1"):
     """Oracle throughput on the host cores at 1 thread and at every core: the
     median of `reps` passes after one warm-up pass, in C_l-sets/s."""
-    smp = OracleSample()
+    smp = OracleSample(workload=workload)
     cores = os.cpu_count() or 1
     res = {}
     for th in (1, cores):
@@ -198,11 +217,12 @@ def cpu_baseline(reps=10):
 
 def run_reference(args):
     """The oracle as it stands on the host cores: each step is one pass over a
-    bounded sample (one cosmology, 16 of the 64 ells), scaled to C_l-sets."""
+    bounded sample of the workload (one cosmology, a subset of its ells; see
+    OracleSample), scaled to C_l-sets."""
     rank, _, world = env_rank()
     if rank != 0:
         return
-    smp = OracleSample(n_req=1)
+    smp = OracleSample(n_req=1, workload=args.workload)
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
         smp.run(cores)
@@ -211,7 +231,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.batch, world),
+            "data": "synthetic", "config": workload_config(args.batch, world, args.workload),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "cpu_model": cpu_model(), "sample": smp.desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -506,8 +526,8 @@ def run_blast(args):
                                 if prof_main[n][1]},
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl == "c1":
-        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(workload=wl)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
