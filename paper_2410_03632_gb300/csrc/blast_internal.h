@@ -98,6 +98,10 @@ struct blast_plan {
     int *d_err = nullptr;           // host-mapped error word written by bounded device waits
     int test_trip = -1;             // test hook of the tensor-core contraction (blast_test_trip_wait)
     int *h_err = nullptr;
+    // side stream of a call: the Chebyshev fit runs there beside the weights
+    // kernel (fork and join through the two events, in the caller's stream order)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     Workspace ws;
 

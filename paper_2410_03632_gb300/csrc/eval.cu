@@ -531,8 +531,14 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
     int *de = reinterpret_cast<int *>(dreq + n);
     BL_CUDA(cudaMemcpyAsync(dreq, hreq.data(), sizeof(ReqDev) * n, cudaMemcpyHostToDevice, s));
     BL_CUDA(cudaMemcpyAsync(de, esel.data(), sizeof(int) * esel.size(), cudaMemcpyHostToDevice, s));
-    if ((rc = prof_launch(p, BLAST_K_FIT, s, [&] { return launch_fit(p, dreq, n, s); }))) return rc;
+    // the fit (latency bound) runs on the plan's side stream beside the weights
+    // kernel (HBM bound); both read the staged descriptors, nothing else shared
+    BL_CUDA(cudaEventRecord(p->ev_fork, s));
+    BL_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0));
+    if ((rc = prof_launch(p, BLAST_K_FIT, p->aux, [&] { return launch_fit(p, dreq, n, p->aux); }))) return rc;
+    BL_CUDA(cudaEventRecord(p->ev_join, p->aux));
     if ((rc = prof_launch(p, BLAST_K_WEIGHTS, s, [&] { return launch_weights(p, dreq, n, prec != BLAST_FP64, s, prec == BLAST_FP64); }))) return rc;
+    BL_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     *dreq_out = dreq;
     *d_esel = de;
     return BLAST_OK;

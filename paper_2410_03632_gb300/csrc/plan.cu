@@ -169,6 +169,11 @@ static void plan_free_device(blast_plan *p)
     p->T64 = nullptr; p->T32 = nullptr; p->Tsl = nullptr; p->scT = nullptr;
     if (p->h_err) cudaFreeHost(p->h_err);
     p->h_err = p->d_err = nullptr;
+    if (p->aux) cudaStreamDestroy(p->aux);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    p->aux = nullptr;
+    p->ev_fork = p->ev_join = nullptr;
     p->ws.in.release(); p->ws.coef.release(); p->ws.wts.release();
     p->ws.ypart.release(); p->ws.cl.release(); p->ws.meta.release(); p->ws.tc.release(); p->ws.nl.release(); p->ws.ns.release();
 }
@@ -309,6 +314,14 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
         return BLAST_EDEVICE;
     }
     *p->h_err = 0;
+    if (cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        plan_free_device(p);
+        delete p;
+        return BLAST_EDEVICE;
+    }
     if ((rc = noalloc_prepare(p->device))) {
         plan_free_device(p);
         delete p;
