@@ -45,6 +45,7 @@ extern "C" {
 
 typedef struct blast_plan blast_plan;
 typedef struct blast_server blast_server;
+typedef struct blast_graph blast_graph;
 
 typedef enum {
     BLAST_OK = 0,
@@ -334,6 +335,31 @@ int blast_submit(blast_server *server, int plan_idx, const blast_request *req, i
 int blast_poll(blast_server *server, uint64_t ticket, double *cl_out, int *done, int64_t timeout_us);
 int blast_server_destroy(blast_server *server);
 size_t blast_server_reserved(const blast_server *server);
+
+/* ---------------------------------------------------------------- batch graphs
+ * One blast_cl_batch call captured into a CUDA graph for repeated launches with
+ * the same buffers (Sec. 3.3: the basis is computed once and every cosmology
+ * reuses it; a sampler evaluates new parameters in the same arrays).
+ * blast_graph_create: reqs[0..n) with device inputs (mem_space 1) and outs[i]
+ *   device arrays [npairs][n_sel] (8-byte aligned), checked as blast_cl_batch
+ *   checks them (BLAST_EINVAL, BLAST_ENOBASIS; BLAST_ETIMEOUT as blast_cl).  It
+ *   stages the request descriptors, allocates a work space the graph owns
+ *   (blast_graph_reserved bytes) and captures the call's kernels; synchronous.
+ *   The pointers, tracer counts, P-table lengths and ell masks of reqs are
+ *   fixed in the graph; the contents of every input array may change between
+ *   launches.  The plan must outlive the graph, and its basis must not be
+ *   replaced or reloaded while the graph exists.
+ * blast_graph_launch: enqueues the kernels on stream (stream ordered; the
+ *   outputs are complete when the stream reaches the end of the launch).
+ *   BLAST_ETIMEOUT when a bounded device wait of an earlier launch or call on
+ *   the plan gave up.  Launches and other calls on the same plan must not
+ *   overlap on the GPU.
+ * blast_graph_destroy: frees the graph and its work space (NULL: EINVAL). */
+int blast_graph_create(blast_plan *plan, int n, const blast_request *reqs, int precision, double *const *outs,
+                       blast_graph **out);
+int blast_graph_launch(blast_graph *graph, void *stream);
+size_t blast_graph_reserved(const blast_graph *graph);
+int blast_graph_destroy(blast_graph *graph);
 
 /* Kernel classes of the evaluation path, for blast_profile_read. */
 #define BLAST_K_FIT 0         /* step (a0): Chebyshev fit */

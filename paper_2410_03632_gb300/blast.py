@@ -101,6 +101,12 @@ def lib():
             L.blast_server_destroy.argtypes = [P]
             L.blast_server_reserved.argtypes = [P]
             L.blast_server_reserved.restype = sz
+            L.blast_graph_create.argtypes = [P, i, ctypes.POINTER(blast_request), i, ctypes.POINTER(P),
+                                             ctypes.POINTER(P)]
+            L.blast_graph_launch.argtypes = [P, P]
+            L.blast_graph_reserved.argtypes = [P]
+            L.blast_graph_reserved.restype = sz
+            L.blast_graph_destroy.argtypes = [P]
             _LIB = L
     return _LIB
 
@@ -232,6 +238,28 @@ def blast_poll(h, ticket, out_ptr, timeout_us=-1):
 
 def blast_server_destroy(h):
     return lib().blast_server_destroy(h)
+
+
+def blast_graph_create(h, reqs, precision, out_ptrs):
+    """Handle of a captured batch (device inputs and outputs)."""
+    n = len(reqs)
+    arr = (blast_request * n)(*reqs)
+    outs = (_vp * n)(*out_ptrs)
+    g = _vp()
+    _check(lib().blast_graph_create(h, n, arr, precision, outs, ctypes.byref(g)), "blast_graph_create")
+    return g
+
+
+def blast_graph_launch(g, stream=None):
+    return lib().blast_graph_launch(g, stream)
+
+
+def blast_graph_reserved(g):
+    return lib().blast_graph_reserved(g)
+
+
+def blast_graph_destroy(g):
+    return lib().blast_graph_destroy(g)
 
 
 def blast_server_reserved(h):

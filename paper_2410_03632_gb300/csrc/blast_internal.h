@@ -181,6 +181,14 @@ bool tc_supported(const blast_plan *p);
 size_t tc_y_bytes(const blast_plan *p, int n, int n_esel);  // R-tile partials of a tensor-core call
 size_t tc_ws_total(const blast_plan *p, int n);  // coefficient slices, scales and chi weights of a call
 int tc_reserve(blast_plan *p, int n);
+// Staging of a batch: checks, ell union, work space, request descriptors on the
+// device; with prep, also the fit and the weights (launch_prep).
+int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, double *const *outs, int out_mem_space,
+                cudaStream_t s, ReqDev **dreq_out, int **d_esel, int *n_esel, std::vector<ReqDev> &hreq,
+                std::vector<char> &direct_out, const double *const *pnl, bool prep);
+int launch_prep(blast_plan *p, ReqDev *dreq, int n, int prec, cudaStream_t s);
+// Steps (a) and (b) of a staged, prepared batch in the plan's work space.
+int launch_cl_kernels(blast_plan *p, ReqDev *dreq, int n, int prec, const int *d_esel, int n_esel, cudaStream_t s);
 // Work space for batches of up to nmax requests with device inputs and outputs,
 // every ell and any precision, allocated now; *bytes = the plan's work space.
 int plan_reserve(blast_plan *p, int nmax, size_t *bytes);

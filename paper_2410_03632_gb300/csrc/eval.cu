@@ -420,9 +420,53 @@ static const void *device_view(const void *hp, int pageable)
     return nullptr;
 }
 
+// The fit (a0) and the quadrature weights of a staged batch: the fit
+// (latency bound) runs on the plan's side stream beside the weights kernel
+// (HBM bound); both read the staged descriptors, nothing else is shared.
+int launch_prep(blast_plan *p, ReqDev *dreq, int n, int prec, cudaStream_t s)
+{
+    int rc;
+    BL_CUDA(cudaEventRecord(p->ev_fork, s));
+    BL_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0));
+    if ((rc = prof_launch(p, BLAST_K_FIT, p->aux, [&] { return launch_fit(p, dreq, n, p->aux); }))) return rc;
+    BL_CUDA(cudaEventRecord(p->ev_join, p->aux));
+    if ((rc = prof_launch(p, BLAST_K_WEIGHTS, s, [&] {
+             return launch_weights(p, dreq, n, prec != BLAST_FP64, s, prec == BLAST_FP64);
+         })))
+        return rc;
+    BL_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    return BLAST_OK;
+}
+
+// Steps (a) and (b) of a staged and prepared batch in the plan's work space.
+int launch_cl_kernels(blast_plan *p, ReqDev *dreq, int n, int prec, const int *d_esel, int n_esel, cudaStream_t s)
+{
+    int rc;
+    if (prec == BLAST_BF16S) {
+        const size_t ybytes = tc_y_bytes(p, n, n_esel);
+        if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
+        if ((rc = prof_launch(p, BLAST_K_CONTRACT_TC, s, [&] {
+                 return launch_contract_tc(p, dreq, n, d_esel, n_esel, p->ws.ypart.p, s);
+             })))
+            return rc;
+        return prof_launch(p, BLAST_K_REDUCE, s, [&] {
+            return launch_reduce_tc(p, dreq, n, d_esel, n_esel, p->ws.ypart.p, s);
+        });
+    }
+    const size_t ybytes = (size_t)n * 3 * n_esel * p->X * p->max_tr * (prec == BLAST_FP64 ? 8 : 4);
+    if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
+    if ((rc = prof_launch(p, BLAST_K_CONTRACT, s, [&] {
+             return launch_contract(p, dreq, n, prec, d_esel, n_esel, p->ws.ypart.p, s);
+         })))
+        return rc;
+    return prof_launch(p, BLAST_K_REDUCE, s, [&] {
+        return launch_reduce(p, dreq, n, prec, d_esel, n_esel, p->ws.ypart.p, s);
+    });
+}
+
 int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, double *const *outs,
                 int out_mem_space, cudaStream_t s, ReqDev **dreq_out, int **d_esel, int *n_esel,
-                std::vector<ReqDev> &hreq, std::vector<char> &direct_out, const double *const *pnl = nullptr)
+                std::vector<ReqDev> &hreq, std::vector<char> &direct_out, const double *const *pnl, bool prep)
 {
     Workspace &ws = p->ws;
     int pageable = 0;
@@ -531,14 +575,7 @@ int stage_batch(blast_plan *p, int n, const blast_request *reqs, int prec, doubl
     int *de = reinterpret_cast<int *>(dreq + n);
     BL_CUDA(cudaMemcpyAsync(dreq, hreq.data(), sizeof(ReqDev) * n, cudaMemcpyHostToDevice, s));
     BL_CUDA(cudaMemcpyAsync(de, esel.data(), sizeof(int) * esel.size(), cudaMemcpyHostToDevice, s));
-    // the fit (latency bound) runs on the plan's side stream beside the weights
-    // kernel (HBM bound); both read the staged descriptors, nothing else shared
-    BL_CUDA(cudaEventRecord(p->ev_fork, s));
-    BL_CUDA(cudaStreamWaitEvent(p->aux, p->ev_fork, 0));
-    if ((rc = prof_launch(p, BLAST_K_FIT, p->aux, [&] { return launch_fit(p, dreq, n, p->aux); }))) return rc;
-    BL_CUDA(cudaEventRecord(p->ev_join, p->aux));
-    if ((rc = prof_launch(p, BLAST_K_WEIGHTS, s, [&] { return launch_weights(p, dreq, n, prec != BLAST_FP64, s, prec == BLAST_FP64); }))) return rc;
-    BL_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    if (prep && (rc = launch_prep(p, dreq, n, prec, s))) return rc;
     *dreq_out = dreq;
     *d_esel = de;
     return BLAST_OK;
@@ -613,35 +650,15 @@ static int cl_impl(blast_plan *p, int n, const blast_request *reqs, int prec, do
     std::vector<ReqDev> hreq;
     std::vector<char> direct_out;
     int rc = stage_batch(p, n, reqs, lmode == 1 ? BLAST_FP64 : prec, outs, out_mem_space, s, &dreq, &d_esel, &n_esel,
-                         hreq, direct_out, pnl);
+                         hreq, direct_out, pnl, true);
     if (rc) return rc;
     if (lmode == 1) {
         if ((rc = prof_launch(p, BLAST_K_REDUCE, s, [&] {
                  return launch_limber(p, dreq, n, d_esel, n_esel, (pnl && pnl[0]) ? 1 : 0, extended, s);
              })))
             return rc;
-    } else if (use_tc) {
-        const size_t ybytes = tc_y_bytes(p, n, n_esel);
-        if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
-        if ((rc = prof_launch(p, BLAST_K_CONTRACT_TC, s, [&] {
-                 return launch_contract_tc(p, dreq, n, d_esel, n_esel, p->ws.ypart.p, s);
-             })))
-            return rc;
-        if ((rc = prof_launch(p, BLAST_K_REDUCE, s, [&] {
-                 return launch_reduce_tc(p, dreq, n, d_esel, n_esel, p->ws.ypart.p, s);
-             })))
-            return rc;
-    } else {
-        const size_t ybytes = (size_t)n * 3 * n_esel * p->X * p->max_tr * (prec == BLAST_FP64 ? 8 : 4);
-        if ((rc = p->ws.ypart.ensure(ybytes))) return rc;
-        if ((rc = prof_launch(p, BLAST_K_CONTRACT, s, [&] {
-                 return launch_contract(p, dreq, n, prec, d_esel, n_esel, p->ws.ypart.p, s);
-             })))
-            return rc;
-        if ((rc = prof_launch(p, BLAST_K_REDUCE, s, [&] {
-                 return launch_reduce(p, dreq, n, prec, d_esel, n_esel, p->ws.ypart.p, s);
-             })))
-            return rc;
+    } else if ((rc = launch_cl_kernels(p, dreq, n, prec, d_esel, n_esel, s))) {
+        return rc;
     }
     if (lmode == 2 && (rc = prof_launch(p, BLAST_K_REDUCE, s, [&] {
                            return launch_limber(p, dreq, n, d_esel, n_esel, 2, 0, s);
@@ -690,7 +707,8 @@ extern "C" int blast_cl_nonsep(blast_plan *p, const blast_request *req, const do
     std::vector<ReqDev> hreq;
     std::vector<char> direct_out;
     double *outs[1] = {cl_out};
-    if ((rc = stage_batch(p, 1, req, BLAST_FP64, outs, out_mem_space, s, &dreq, &d_esel, &n_esel, hreq, direct_out)))
+    if ((rc = stage_batch(p, 1, req, BLAST_FP64, outs, out_mem_space, s, &dreq, &d_esel, &n_esel, hreq, direct_out,
+                          nullptr, true)))
         return rc;
     const size_t qn = (size_t)p->Q * p->N;
     if ((rc = p->ws.ns.ensure(2 * qn * sizeof(double)))) return rc;
