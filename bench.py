@@ -182,9 +182,10 @@ class OracleSample:
                 self.items.append((rq, list(range(sub_idx.size)), sub_idx.size / spec.ells.size))
         self.sub = spec.ells[sub_idx]
         self.sets = sum(f for _, _, f in self.items)  # C_l-sets one run evaluates
-        self.desc = (f"{workload}: {n_req} cosmologies x every {stride}th of the {spec.ells.size} ells "
-                     f"(within each request's own ell set for c3) on the {grid} grid, oracle fit + contraction "
-                     f"+ quadrature, seeded random basis of the right shape; scaled to full C_l-sets")
+        own = " (those within each request's own ell set)" if workload == "c3" else ""
+        self.desc = (f"{workload}: {n_req} cosmologies x every {stride}th of the {spec.ells.size} ells{own} "
+                     f"on the {grid} grid, oracle fit + contraction + quadrature, seeded random basis of the "
+                     f"right shape; scaled to full C_l-sets")
 
     def run(self, threads):
         """Seconds for one pass over the sample with `threads` OpenMP threads."""
@@ -257,16 +258,18 @@ def alu_peaks():
 
 
 # --------------------------------------------------------------------------- GPU arm
-def traffic_for(kernel_file, kernel_name):
+def traffic_for(kernel_file, kernel_name, workload="c1", batch=256):
     """ncu DRAM bytes per launch recorded in profiles/traffic.json for the
-    current source of the kernel (None when the source changed since)."""
+    current source of the kernel and this workload and batch (None when the
+    source changed since or no capture covers the workload)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     src = open(os.path.join(ROOT, "paper_2410_03632_gb300", "csrc", kernel_file), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
     for rec in json.load(open(path)):
-        if rec.get("kernel") == kernel_name and rec.get("src_sha") == sha:
+        if (rec.get("kernel") == kernel_name and rec.get("src_sha") == sha and rec.get("workload") == workload
+                and rec.get("batch") == batch):
             return rec.get("bytes_per_launch_full")
     return None
 
@@ -427,7 +430,7 @@ def run_blast(args):
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "peak_kind": "bf16 burst, of measured",
                 "flops_per_launch": flops, "flops_def": "2*3*L*N*Q*B x3 (split-MMA allowance)",
-                "traffic": traffic_for("contract_tc.cu", "contract_tc"),
+                "traffic": traffic_for("contract_tc.cu", "contract_tc", wl, B),
                 "slice_mma": {"achieved": slice_rate, "frac": slice_rate / peak, "flops_per_launch": slice_flops,
                               "def": "15 BF16 slice products per product, K padded to 64, M padded to 128"}}
     else:
@@ -436,7 +439,7 @@ def run_blast(args):
         peak = peaks.get("hbm_gbs", 6800.0)
         achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_kind": "hbm copy, of measured", "traffic": traffic_for("eval.cu", "k_contract<float>")}
+                "peak_kind": "hbm copy, of measured", "traffic": traffic_for("eval.cu", "k_contract<float>", wl, B)}
     roof["kernel"] = kname
     roof["avg_launch_ms"] = avg_ms
     roof["launches"] = klaunch
