@@ -54,18 +54,19 @@ def lib():
             L.orc_cc_grid.argtypes = [i, d, d, _dp, _dp, _dp, i]
             L.orc_cheb_knodes.argtypes = [i, d, d, i, _dp, _dp]
             L.orc_jl.argtypes = [i, d, _dp]
-            L.orc_basis.argtypes = [i, _ip, i, _dp, _dp, i, d, d, i, i, i, _dp]
+            L.orc_basis.argtypes = [i, _dp, i, _dp, _dp, i, d, d, i, i, i, _dp]
+            L.orc_jnu.argtypes = [d, d, _dp]
             L.orc_cheb_dct.argtypes = [i, _dp, _dp]
             L.orc_spline_natural.argtypes = [i, _dp, _dp, i, _dp, _dp]
             L.orc_fit.argtypes = [i, d, d, i, i, _dp, _dp, _dp]
-            L.orc_prefactor.argtypes = [i, i]
+            L.orc_prefactor.argtypes = [i, d]
             L.orc_prefactor.restype = d
             L.orc_npairs.argtypes = [i, i]
-            L.orc_cl.argtypes = [i, _ip, i, i, _dp, _dp, _dp, _dp, i, _dp, _dp, i, i,
+            L.orc_cl.argtypes = [i, _dp, i, i, _dp, _dp, _dp, _dp, i, _dp, _dp, i, i,
                                  _dp, _dp, _dp, _dp, _dp, i, i]
-            L.orc_limber.argtypes = [i, _ip, i, _dp, _dp, i, i, _dp, _dp, _dp, i, _dp]
-            L.orc_cl_nonsep.argtypes = [i, _ip, i, i, _dp, _dp, _dp, i, _dp, _dp, i, i, _dp, _dp, _dp]
-            L.orc_limber_plin.argtypes = [i, _ip, i, _dp, _dp, i, _dp, _dp, _dp]
+            L.orc_limber.argtypes = [i, _dp, i, _dp, _dp, i, i, _dp, _dp, _dp, i, _dp]
+            L.orc_cl_nonsep.argtypes = [i, _dp, i, i, _dp, _dp, _dp, i, _dp, _dp, i, i, _dp, _dp, _dp]
+            L.orc_limber_plin.argtypes = [i, _dp, i, _dp, _dp, i, _dp, _dp, _dp]
             _LIB = L
     return _LIB
 
@@ -124,10 +125,17 @@ def jl(lmax, x):
     return out
 
 
+def jnu(nu, x):
+    """Spherical Bessel j_nu(x) of real order nu >= 0."""
+    out = np.empty(1)
+    _check(lib().orc_jnu(float(nu), float(x), _d(out)[1]), "jnu")
+    return float(out[0])
+
+
 # --------------------------------------------------------------------------- basis
 def basis(ells, chi1, chi2, N, kmin, kmax, Nk, kmap=0, nthreads=0):
     """T~[t][e][n][q] for point pairs (chi1[q], chi2[q]); t = gg, gs, ss."""
-    ells, pe = _i(ells)
+    ells, pe = _d(ells)
     chi1, p1 = _d(chi1)
     chi2, p2 = _d(chi2)
     nq = chi1.size
@@ -162,7 +170,7 @@ def fit(N, kmin, kmax, ktab, ptab, kmap=0):
 
 
 def prefactor(t, ell):
-    return lib().orc_prefactor(int(t), int(ell))
+    return lib().orc_prefactor(int(t), float(ell))
 
 
 def npairs(ng, ns):
@@ -174,7 +182,7 @@ def cl(ells, chi, wchi, R, wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, nthreads=
     """C[p][e] from T~[3][n_ell][N][X*Rn] and the fitted a_n (steps 5-6);
     nthreads 0 = every OpenMP thread (independent (type, ell) items); sym: the
     symmetrised form of App. A (R in (0, 1], both kernel orders)."""
-    ells, pe = _i(ells)
+    ells, pe = _d(ells)
     chi, pc = _d(chi)
     wchi, pwc = _d(wchi)
     R, pR = _d(R)
@@ -197,7 +205,7 @@ def cl(ells, chi, wchi, R, wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, nthreads=
 # --------------------------------------------------------------------------- Limber
 def limber(ells, chi, wchi, ng, ns, kchi, Dchi, P, extended=False):
     """Limber (or extended Limber) C[p][e] on the chi rule, P[e][a] = P(nu/chi_a, chi_a)."""
-    ells, pe = _i(ells)
+    ells, pe = _d(ells)
     chi, pc = _d(chi)
     wchi, pw = _d(wchi)
     kchi, pk = _d(kchi)
@@ -212,7 +220,7 @@ def limber(ells, chi, wchi, ng, ns, kchi, Dchi, P, extended=False):
 
 def limber_plin(ells, chi, Dchi, ktab, ptab):
     """D(chi_a)^2 P(nu/chi_a) from a P table (natural spline in (ln k, ln P)), [e][a]."""
-    ells, pe = _i(ells)
+    ells, pe = _d(ells)
     chi, pc = _d(chi)
     Dchi, pD = _d(Dchi)
     ktab, pk = _d(ktab)
@@ -225,7 +233,7 @@ def limber_plin(ells, chi, Dchi, ktab, ptab):
 def cl_nonsep(ells, chi, wchi, wR, T, Pq, ng, ns, kchi, kRchi):
     """C[p][e] for a non-separable P sampled at the Chebyshev k-nodes of every
     chi-R node, Pq[q][j] (q = a n_R + r)."""
-    ells, pe = _i(ells)
+    ells, pe = _d(ells)
     chi, pc = _d(chi)
     wchi, pw = _d(wchi)
     wR, pwR = _d(wR)
@@ -248,7 +256,7 @@ class Grid:
     def __init__(self, ells, X, chi_min, chi_max, Rn, R_min, R_max, N, k_min, k_max, Nk, k_map=0, r_form=0):
         """r_form 0: R in [R_min, R_max] (two panels meeting at R = 1); 1: the
         symmetrised form on (0, 1] (App. A; R_min, R_max unused)."""
-        self.ells = np.asarray(ells, dtype=np.int32)
+        self.ells = np.asarray(ells, dtype=np.float64)
         self.X, self.Rn, self.N, self.Nk, self.k_map = X, Rn, N, Nk, k_map
         self.k_min, self.k_max = k_min, k_max
         self.r_form = int(r_form)
@@ -258,7 +266,7 @@ class Grid:
         self.chi2 = (self.chi[:, None] * self.R[None, :]).ravel()
 
     def basis(self, ell_subset=None, nthreads=0):
-        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
+        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.float64)
         return basis(ells, self.chi1, self.chi2, self.N, self.k_min, self.k_max, self.Nk,
                      self.k_map, nthreads)
 
@@ -268,18 +276,18 @@ class Grid:
     def cl_nonsep(self, T, Pq, ng, ns, kchi, kRchi, ell_subset=None):
         if self.r_form:
             raise NotImplementedError("the non-separable oracle uses the R in [R_min, R_max] form")
-        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
+        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.float64)
         return cl_nonsep(ells, self.chi, self.wchi, self.wR, T, Pq, ng, ns, kchi, kRchi)
 
     def limber(self, ng, ns, kchi, Dchi, P, extended=False, ell_subset=None):
-        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
+        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.float64)
         return limber(ells, self.chi, self.wchi, ng, ns, kchi, Dchi, P, extended)
 
     def limber_plin(self, Dchi, ktab, ptab, ell_subset=None):
-        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
+        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.float64)
         return limber_plin(ells, self.chi, Dchi, ktab, ptab)
 
     def cl(self, T, a, ng, ns, kchi, kRchi, Dchi, DRchi, ell_subset=None, nthreads=0):
-        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.int32)
+        ells = self.ells if ell_subset is None else np.asarray(ell_subset, dtype=np.float64)
         return cl(ells, self.chi, self.wchi, self.R, self.wR, T, a, ng, ns, kchi, kRchi, Dchi, DRchi,
                   nthreads, sym=self.r_form == 1)

@@ -235,6 +235,53 @@ int orc_jl(int lmax, double x, double *j)
 }
 
 /* ------------------------------------------------------------------------- */
+/* j_nu(x) for real nu >= 0 (non-integer multipoles, App. A's l = 211.63):    */
+/*   j_nu(x) = sqrt(pi / (2x)) J_{nu+1/2}(x).                                */
+/* J by Miller's backward recurrence J_{m-1} = (2m/x) J_m - J_{m+1} on the   */
+/* orders m = mu0 + k (mu0 = frac(nu + 1/2)), from k = K well above x and    */
+/* nu + 1/2, normalised by Neumann's expansion                                */
+/*   (x/2)^mu0 = sum_{i>=0} (mu0 + 2i) Gamma(mu0 + i) / i! J_{mu0+2i}(x)      */
+/* (the i = 0 term is Gamma(mu0 + 1) J_mu0).                                 */
+/* ------------------------------------------------------------------------- */
+int orc_jnu(double nu, double x, double *out)
+{
+    if (!(nu >= 0.0) || !(x >= 0.0) || isinf(x) || isinf(nu)) return -1;
+    if (x == 0.0) { *out = (nu == 0.0) ? 1.0 : 0.0; return 0; }
+    const double mu = nu + 0.5;
+    const int nmu = (int)floor(mu);
+    const double mu0 = mu - (double)nmu;
+    const double top = (double)nmu > x ? (double)nmu : x;
+    const int K = (int)top + 40 + (int)(10.0 * cbrt(top));
+    /* Neumann weights c_i = (mu0 + 2i) Gamma(mu0 + i) / i!, upward from
+     * Gamma(mu0 + 1) with the exact ratios (mu0 + i) / (i + 1), in long double */
+    const int I = K / 2;
+    long double *c = (long double *)malloc(sizeof(long double) * (I + 1));
+    if (!c) return -2;
+    long double g = (long double)tgamma(mu0 + 1.0); /* Gamma(mu0 + 1) / 1! = Gamma(mu0 + i) / i! at i = 1 */
+    c[0] = g;                                        /* mu0 Gamma(mu0) = Gamma(mu0 + 1) */
+    for (int i = 1; i <= I; i++) {
+        c[i] = ((long double)mu0 + 2.0L * i) * g;
+        g *= ((long double)mu0 + i) / ((long double)i + 1.0L);
+    }
+    double fp = 0.0, f = 1e-280, rec = 0.0;
+    long double S = 0.0L;
+    for (int k = K; k >= 0; k--) {
+        /* f = J_{mu0+k} (unnormalised), fp = J_{mu0+k+1} */
+        if (k == nmu) rec = f;
+        if (k % 2 == 0) S += c[k / 2] * (long double)f;
+        if (k == 0) break;
+        double fm = 2.0 * (mu0 + k) / x * f - fp;
+        fp = f;
+        f = fm;
+        if (fabs(f) > 1e250) { f *= 1e-250; fp *= 1e-250; S *= 1e-250L; rec *= 1e-250; }
+    }
+    free(c);
+    double J = (double)((long double)rec * (long double)pow(0.5 * x, mu0) / S);
+    *out = sqrt(ORC_PI / (2.0 * x)) * J;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Basis integrals, Eq. t_tilde:                                             */
 /*   T~^{AB}_{n;l}(chi1, chi2) = int_{kmin}^{kmax} dk f^{AB}(k) T_n(x(k))      */
 /*                                 j_l(k chi1) j_l(k chi2)                    */
@@ -245,14 +292,15 @@ int orc_jl(int lmax, double x, double *j)
 /* Output T[t][e][n][q] for the ells ell[0..n_ell) and point pairs            */
 /* (chi1[q], chi2[q]), q < nq.                                               */
 /* ------------------------------------------------------------------------- */
-int orc_basis(int n_ell, const int *ell, int nq, const double *chi1, const double *chi2,
+int orc_basis(int n_ell, const double *ell, int nq, const double *chi1, const double *chi2,
               int N, double kmin, double kmax, int kmap, int Nk, int nthreads, double *T)
 {
     if (n_ell < 1 || nq < 1 || N < 1 || !(kmin > 0.0) || kmap < 0 || kmap > 1) return -1;
-    int lmax = 0;
+    int lmax = 0, integer = 1;
     for (int e = 0; e < n_ell; e++) {
-        if (ell[e] < 0) return -1;
-        if (ell[e] > lmax) lmax = ell[e];
+        if (!(ell[e] >= 0.0)) return -1;
+        if (ell[e] != floor(ell[e])) integer = 0;
+        if ((int)ceil(ell[e]) > lmax) lmax = (int)ceil(ell[e]);
     }
     double *k = (double *)malloc(sizeof(double) * Nk);
     double *x = (double *)malloc(sizeof(double) * Nk);
@@ -294,9 +342,18 @@ int orc_basis(int n_ell, const int *ell, int nq, const double *chi1, const doubl
             memset(acc, 0, per_q * sizeof(double));
             memset(cmp, 0, per_q * sizeof(double));
             for (int m = 0; m < Nk; m++) {
-                orc_jl(lmax, k[m] * chi1[q], b1);
-                orc_jl(lmax, k[m] * chi2[q], b2);
-                for (int e = 0; e < n_ell; e++) bm[e] = b1[ell[e]] * b2[ell[e]];
+                if (integer) {  /* one ladder of integer orders serves every ell */
+                    orc_jl(lmax, k[m] * chi1[q], b1);
+                    orc_jl(lmax, k[m] * chi2[q], b2);
+                    for (int e = 0; e < n_ell; e++) bm[e] = b1[(int)ell[e]] * b2[(int)ell[e]];
+                } else {
+                    for (int e = 0; e < n_ell; e++) {
+                        double u, v;
+                        orc_jnu(ell[e], k[m] * chi1[q], &u);
+                        orc_jnu(ell[e], k[m] * chi2[q], &v);
+                        bm[e] = u * v;
+                    }
+                }
                 for (int t = 0; t < 3; t++) {
                     const double *Am = A + ((size_t)m * 3 + t) * N;
                     for (int e = 0; e < n_ell; e++) {
@@ -413,9 +470,9 @@ int orc_fit(int N, double kmin, double kmax, int kmap, int ntab, const double *k
 /* Prefactors N(l) of Eqs. gg, gs, ss: 2/pi, (2/pi) sqrt((l+2)!/(l-2)!),     */
 /* (2/pi) (l+2)!/(l-2)!, with (l+2)!/(l-2)! = (l+2)(l+1) l (l-1).            */
 /* ------------------------------------------------------------------------- */
-double orc_prefactor(int type, int l)
+double orc_prefactor(int type, double l)
 {
-    double L = (double)l;
+    double L = l;
     double r = (L + 2.0) * (L + 1.0) * L * (L - 1.0);
     if (type == 0) return 2.0 / ORC_PI;
     if (type == 1) return 2.0 / ORC_PI * sqrt(r);
@@ -443,7 +500,7 @@ int orc_npairs(int ng, int ns)
 /*   C = N_AB sum_a sum_r wchi_a wR_r chi_a                                  */
 /*       [K^A_i(chi_a) K^B_j(R_r chi_a) + K^B_j(chi_a) K^A_i(R_r chi_a)] w    */
 /* (the kernels at chi_a are the rows of kchi, at R_r chi_a those of kRchi). */
-int orc_cl(int n_ell, const int *ell, int X, int Rn, const double *chi, const double *wchi,
+int orc_cl(int n_ell, const double *ell, int X, int Rn, const double *chi, const double *wchi,
            const double *R, const double *wR, int N, const double *T, const double *a,
            int ng, int ns, const double *kchi, const double *kRchi,
            const double *Dchi, const double *DRchi, double *C, int nthreads, int sym)
@@ -548,7 +605,7 @@ static void orc_fd_derivs(int X, double h, const double *f, double *d2, double *
     }
 }
 
-int orc_limber(int n_ell, const int *ell, int X, const double *chi, const double *wchi, int ng, int ns,
+int orc_limber(int n_ell, const double *ell, int X, const double *chi, const double *wchi, int ng, int ns,
                const double *kchi, const double *Dchi, const double *P, int extended, double *C)
 {
     if (n_ell < 1 || X < 5 || ng < 0 || ns < 0 || ng + ns < 1) return -1;
@@ -602,7 +659,7 @@ int orc_limber(int n_ell, const int *ell, int X, const double *chi, const double
  * D(chi_a)^2 P(k), P(k) from the request's table by the natural cubic spline
  * of (ln k, ln P) that the fit uses (orc_spline_natural), zero where k lies
  * outside the table. */
-int orc_limber_plin(int n_ell, const int *ell, int X, const double *chi, const double *Dchi, int ntab,
+int orc_limber_plin(int n_ell, const double *ell, int X, const double *chi, const double *Dchi, int ntab,
                     const double *ktab, const double *ptab, double *P)
 {
     if (n_ell < 1 || X < 1 || ntab < 3) return -1;
@@ -640,7 +697,7 @@ int orc_limber_plin(int n_ell, const int *ell, int X, const double *chi, const d
 /* replaces D(chi_a) D(R_r chi_a) sum_n a_n T~; the chi-R quadrature is that */
 /* of orc_cl with the kernels K alone.  Output C[p][e].                      */
 /* ------------------------------------------------------------------------- */
-int orc_cl_nonsep(int n_ell, const int *ell, int X, int Rn, const double *chi, const double *wchi,
+int orc_cl_nonsep(int n_ell, const double *ell, int X, int Rn, const double *chi, const double *wchi,
                   const double *wR, int N, const double *T, const double *Pq, int ng, int ns,
                   const double *kchi, const double *kRchi, double *C)
 {
