@@ -80,7 +80,12 @@ typedef enum {
 #define BLAST_BASIS_BF16S (1u << 2)  /* slice tables of the tensor-core path */
 
 /* Grid and size description of a plan (Sec. 3.2 of the paper).
- *   ell      n_ell integer multipoles, 2 <= ell, strictly increasing, n_ell <= 128
+ *   ell      n_ell integer multipoles, 2 <= ell, strictly increasing, n_ell <= 128;
+ *            ignored when ell_real is set
+ *   ell_real NULL, or n_ell real multipoles, 2 <= ell <= 1e5, strictly increasing
+ *            (App. A evaluates the basis at l = 211.63): the basis uses spherical
+ *            Bessel functions of that real order, N_AB(l) and the Limber terms
+ *            take l as given.  Integer values give the integer plan exactly.
  *   chi      n_chi evenly spaced nodes on [chi_min, chi_max], composite Simpson
  *            weights (3/8 rule on the last three intervals when n_chi is even)
  *   R        r_form 0 (the split form, chi2 = R chi1 with R in [R_min, R_max]):
@@ -113,6 +118,7 @@ typedef struct {
     int max_clust, max_lens;
     int device;
     int r_form;
+    const double *ell_real;
 } blast_plan_desc;
 
 /* One cosmology.  Tracers 0..n_clust-1 are clustering, n_clust..n_clust+n_lens-1

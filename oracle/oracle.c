@@ -253,30 +253,36 @@ int orc_jnu(double nu, double x, double *out)
     const double top = (double)nmu > x ? (double)nmu : x;
     const int K = (int)top + 40 + (int)(10.0 * cbrt(top));
     /* Neumann weights c_i = (mu0 + 2i) Gamma(mu0 + i) / i!, upward from
-     * Gamma(mu0 + 1) with the exact ratios (mu0 + i) / (i + 1), in long double */
+     * Gamma(mu0 + 1) with the exact ratios (mu0 + i) / (i + 1) (one rounding
+     * per step), in a per-thread buffer */
+    static _Thread_local double *cbuf = NULL;
+    static _Thread_local int ccap = 0;
     const int I = K / 2;
-    long double *c = (long double *)malloc(sizeof(long double) * (I + 1));
-    if (!c) return -2;
-    long double g = (long double)tgamma(mu0 + 1.0); /* Gamma(mu0 + 1) / 1! = Gamma(mu0 + i) / i! at i = 1 */
-    c[0] = g;                                        /* mu0 Gamma(mu0) = Gamma(mu0 + 1) */
-    for (int i = 1; i <= I; i++) {
-        c[i] = ((long double)mu0 + 2.0L * i) * g;
-        g *= ((long double)mu0 + i) / ((long double)i + 1.0L);
+    if (I + 1 > ccap) {
+        double *nb = (double *)realloc(cbuf, sizeof(double) * (size_t)(I + 1));
+        if (!nb) return -2;
+        cbuf = nb;
+        ccap = I + 1;
     }
-    double fp = 0.0, f = 1e-280, rec = 0.0;
-    long double S = 0.0L;
+    double *c = cbuf;
+    double g = tgamma(mu0 + 1.0); /* Gamma(mu0 + i) / i! at i = 1 */
+    c[0] = g;                     /* mu0 Gamma(mu0) = Gamma(mu0 + 1) */
+    for (int i = 1; i <= I; i++) {
+        c[i] = (mu0 + 2.0 * i) * g;
+        g *= (mu0 + i) / (i + 1.0);
+    }
+    double fp = 0.0, f = 1e-280, rec = 0.0, S = 0.0;
     for (int k = K; k >= 0; k--) {
         /* f = J_{mu0+k} (unnormalised), fp = J_{mu0+k+1} */
         if (k == nmu) rec = f;
-        if (k % 2 == 0) S += c[k / 2] * (long double)f;
+        if (k % 2 == 0) S += c[k / 2] * f;
         if (k == 0) break;
         double fm = 2.0 * (mu0 + k) / x * f - fp;
         fp = f;
         f = fm;
-        if (fabs(f) > 1e250) { f *= 1e-250; fp *= 1e-250; S *= 1e-250L; rec *= 1e-250; }
+        if (fabs(f) > 1e250) { f *= 1e-250; fp *= 1e-250; S *= 1e-250; rec *= 1e-250; }
     }
-    free(c);
-    double J = (double)((long double)rec * (long double)pow(0.5 * x, mu0) / S);
+    double J = rec * pow(0.5 * x, mu0) / S;
     *out = sqrt(ORC_PI / (2.0 * x)) * J;
     return 0;
 }

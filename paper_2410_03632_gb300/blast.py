@@ -36,7 +36,7 @@ class blast_plan_desc(ctypes.Structure):
                 ("n_cheb", ctypes.c_int), ("k_min", ctypes.c_double), ("k_max", ctypes.c_double),
                 ("k_map", ctypes.c_int), ("n_kquad", ctypes.c_int),
                 ("max_clust", ctypes.c_int), ("max_lens", ctypes.c_int), ("device", ctypes.c_int),
-                ("r_form", ctypes.c_int)]
+                ("r_form", ctypes.c_int), ("ell_real", ctypes.POINTER(ctypes.c_double))]
 
 
 class blast_request(ctypes.Structure):
@@ -313,10 +313,14 @@ class Plan:
     def __init__(self, spec, device: int = 0):
         self.spec = spec
         self.device = device
-        self._ell = np.ascontiguousarray(spec.ells, dtype=np.int32)
+        ells = np.asarray(spec.ells)
+        self._ellr = np.ascontiguousarray(ells, dtype=np.float64)
+        self._ell = np.ascontiguousarray(np.floor(self._ellr), dtype=np.int32)
         d = blast_plan_desc()
         d.n_ell = self._ell.size
         d.ell = self._ell.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        if np.any(self._ellr != np.floor(self._ellr)):  # non-integer multipoles
+            d.ell_real = self._ellr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         d.n_chi, d.chi_min, d.chi_max = spec.n_chi, spec.chi_min, spec.chi_max
         d.n_R, d.R_min, d.R_max = spec.n_R, spec.R_min, spec.R_max
         d.n_cheb, d.k_min, d.k_max, d.k_map = spec.n_cheb, spec.k_min, spec.k_max, spec.k_map

@@ -67,7 +67,8 @@ struct Workspace {
 
 struct blast_plan {
     // description (ells copied)
-    std::vector<int32_t> ell;
+    std::vector<double> ell;        // multipoles (integers, or real values: real_ell)
+    bool real_ell = false;
     int L = 0, X = 0, Rn = 0, Q = 0, N = 0, Nk = 0, kmap = 0;
     int r_form = 0;  // 0: R in [R_min, R_max]; 1: symmetrised form on (0, 1]
     double chi_min = 0, chi_max = 0, R_min = 0, R_max = 0, k_min = 0, k_max = 0;
@@ -83,7 +84,7 @@ struct blast_plan {
     double *d_kcheb_u = nullptr;   // ln k of each Chebyshev node
     double *d_cos_tab = nullptr;   // cos(pi p / 2N), p < 4N
     double *d_pref = nullptr;      // N_AB(l) [3][L]
-    int32_t *d_ell = nullptr;      // the plan's ells
+    double *d_ell = nullptr;       // the plan's ells
     std::vector<double> env;       // power-of-two coefficient envelope s_n of the tensor-core path
     double *d_env = nullptr;
 

@@ -742,7 +742,7 @@ extern "C" int blast_limber_k(const blast_plan *p, double *k)
 {
     if (!p || !k) return BLAST_EINVAL;
     for (int e = 0; e < p->L; e++)
-        for (int a = 0; a < p->X; a++) k[(size_t)e * p->X + a] = ((double)p->ell[e] + 0.5) / p->chi[a];
+        for (int a = 0; a < p->X; a++) k[(size_t)e * p->X + a] = (p->ell[e] + 0.5) / p->chi[a];
     return BLAST_OK;
 }
 

@@ -48,7 +48,7 @@ __device__ double spline_P(const ReqDev &rq, double k)
 // tracer weights in shared memory, then one thread per tracer pair.
 __global__ void __launch_bounds__(kLimThreads)
 k_limber(const ReqDev *__restrict__ reqs, const double *__restrict__ chi, const double *__restrict__ wchi, int X,
-         const int *__restrict__ esel, const int32_t *__restrict__ ell, int mode, int extended)
+         const int *__restrict__ esel, const double *__restrict__ ell, int mode, int extended)
 {
     extern __shared__ double lsm[];
     const ReqDev &rq = reqs[blockIdx.y];
@@ -60,7 +60,7 @@ k_limber(const ReqDev *__restrict__ reqs, const double *__restrict__ chi, const 
     double *W = Pv + X;               // [ntr][X]
     double *K2 = W + (size_t)ntr * X; // [ntr][X] Kt'' (extended only)
     double *K3 = K2 + (size_t)ntr * X;
-    const double l = (double)ell[e], nu = l + 0.5;
+    const double l = ell[e], nu = l + 0.5;
     for (int a = threadIdx.x; a < X; a += blockDim.x) {
         const double c = chi[a], k = nu / c, D2 = rq.growth_chi[a] * rq.growth_chi[a];
         double v;

@@ -182,10 +182,11 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
 {
     if (!d || !out) return BLAST_EINVAL;
     *out = nullptr;
-    if (d->n_ell < 1 || d->n_ell > BLAST_MAX_ELL || !d->ell) return BLAST_EINVAL;
+    if (d->n_ell < 1 || d->n_ell > BLAST_MAX_ELL || (!d->ell && !d->ell_real)) return BLAST_EINVAL;
     for (int e = 0; e < d->n_ell; e++) {
-        if (d->ell[e] < 2) return BLAST_EINVAL;
-        if (e && d->ell[e] <= d->ell[e - 1]) return BLAST_EINVAL;
+        const double l = d->ell_real ? d->ell_real[e] : (double)d->ell[e];
+        if (!(l >= 2.0) || !(l <= 1e5)) return BLAST_EINVAL;
+        if (e && !(l > (d->ell_real ? d->ell_real[e - 1] : (double)d->ell[e - 1]))) return BLAST_EINVAL;
     }
     if (d->n_chi < 4 || !(d->chi_min > 0) || !(d->chi_max > d->chi_min)) return BLAST_EINVAL;
     if (d->r_form != 0 && d->r_form != 1) return BLAST_EINVAL;
@@ -201,7 +202,11 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
 
     blast_plan *p = new (std::nothrow) blast_plan();
     if (!p) return BLAST_ENOMEM;
-    p->ell.assign(d->ell, d->ell + d->n_ell);
+    p->ell.resize(d->n_ell);
+    for (int e = 0; e < d->n_ell; e++) {
+        p->ell[e] = d->ell_real ? d->ell_real[e] : (double)d->ell[e];
+        if (p->ell[e] != floor(p->ell[e])) p->real_ell = true;
+    }
     p->L = d->n_ell; p->X = d->n_chi; p->Rn = d->n_R; p->Q = d->n_chi * d->n_R;
     p->N = d->n_cheb; p->Nk = d->n_kquad; p->kmap = d->k_map;
     p->chi_min = d->chi_min; p->chi_max = d->chi_max; p->R_min = d->R_min; p->R_max = d->R_max;
@@ -278,7 +283,7 @@ extern "C" int blast_plan_create(const blast_plan_desc *d, blast_plan **out)
     for (int m = 0; m <= nq; m++) { p->kq[m] = kc + kh * cx[m]; p->wq[m] = kh * cw[m]; }
 
     // grid hash (for basis files)
-    uint64_t hsh = fnv1a(p->ell.data(), sizeof(int32_t) * p->L);
+    uint64_t hsh = fnv1a(p->ell.data(), sizeof(double) * p->L);
     double dv[6] = {p->chi_min, p->chi_max, p->R_min, p->R_max, p->k_min, p->k_max};
     int iv[6] = {p->X, p->Rn, p->N, p->Nk, p->kmap, p->r_form};
     hsh = fnv1a(dv, sizeof dv, hsh);

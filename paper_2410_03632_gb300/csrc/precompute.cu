@@ -99,10 +99,127 @@ __device__ void jl_group(double x, const int *lg, int ng, double *out)
     for (int g = 0; g < kG; g++) out[g] *= scale;
 }
 
+// j_v0(x) and j_v0+1(x) for a fractional order v0 in [0, 1) (non-integer
+// multipoles), j_v = sqrt(pi / 2x) J_{v+1/2}:
+// x >= 30: Hankel's asymptotic expansion, j_v = (P cos w - Q sin w) / x with
+//   w = x - (v + 1) pi / 2 (formed by angle addition from sincos(x), which
+//   keeps the phase exact for large x), P and Q the even and odd terms of
+//   a_k = (m - 1)(m - 9)...(m - (2k-1)^2) / (k! (8x)^k), m = 4 (v + 1/2)^2;
+// 1e-3 <= x < 30: Miller's backward recurrence on J_{mu0 + k}, mu0 =
+//   frac(v0 + 1/2), normalised by Neumann's expansion
+//   (x/2)^mu0 = sum_i (mu0 + 2i) Gamma(mu0 + i) / i! J_{mu0 + 2i};
+// x < 1e-3: the first three terms of the power series.
+__device__ void jnu_start(double v0, double x, double &j0, double &j1)
+{
+    const double mu = v0 + 0.5;
+    if (x >= 30.0) {
+        double sx, cx;
+        sincos(x, &sx, &cx);
+        double out[2];
+#pragma unroll
+        for (int o = 0; o < 2; o++) {
+            const double v = v0 + o, m = 4.0 * (v + 0.5) * (v + 0.5);
+            double P = 1.0, Qs = 0.0, t = 1.0;
+            for (int k = 1; k < 60; k++) {
+                const double c = (double)(2 * k - 1);
+                const double tn = t * (m - c * c) / ((double)k * 8.0 * x);
+                if (fabs(tn) > fabs(t) && k > 2) break;  // the asymptotic terms start to grow
+                t = tn;
+                const int r = k & 3;  // signs: k = 1 +Q, 2 -P, 3 -Q, 4 +P
+                if (r == 1) Qs += t;
+                else if (r == 2) P -= t;
+                else if (r == 3) Qs -= t;
+                else P += t;
+                if (fabs(t) < 1e-18) break;
+            }
+            double sp, cp;  // phase (v + 1) pi / 2
+            sincospi(0.5 * (v + 1.0), &sp, &cp);
+            const double cw = cx * cp + sx * sp, sw = sx * cp - cx * sp;
+            out[o] = (P * cw - Qs * sw) / x;
+        }
+        j0 = out[0];
+        j1 = out[1];
+        return;
+    }
+    const double pre = sqrt(0.5 * 3.14159265358979323846 / x);
+    if (x < 1e-3) {
+#pragma unroll
+        for (int o = 0; o < 2; o++) {
+            const double m = mu + o, h = 0.25 * x * x;
+            const double J = pow(0.5 * x, m) / tgamma(m + 1.0) * (1.0 - h / (m + 1.0) + h * h / (2.0 * (m + 1.0) * (m + 2.0)));
+            (o ? j1 : j0) = pre * J;
+        }
+        return;
+    }
+    const int nb = (int)floor(mu);
+    const double mu0 = mu - nb;
+    const int K = (int)x + 40;  // <= 69
+    double c[36];               // Neumann weights for k = 2i <= K
+    double g = tgamma(mu0 + 1.0);
+    c[0] = g;
+    for (int i = 1; i <= K / 2; i++) {
+        c[i] = (mu0 + 2.0 * i) * g;
+        g *= (mu0 + i) / (i + 1.0);
+    }
+    double fp = 0.0, f = 1e-250, S = 0.0, r0 = 0.0, r1 = 0.0;
+    for (int k = K; k >= 0; k--) {
+        if (k == nb) r0 = f;
+        if (k == nb + 1) r1 = f;
+        if ((k & 1) == 0) S += c[k / 2] * f;
+        if (k == 0) break;
+        const double fm = 2.0 * (mu0 + k) / x * f - fp;
+        fp = f;
+        f = fm;
+        if (fabs(f) > 1e200) { f *= 1e-200; fp *= 1e-200; S *= 1e-200; r0 *= 1e-200; r1 *= 1e-200; }
+    }
+    const double nrm = pow(0.5 * x, mu0) / S;
+    j0 = pre * r0 * nrm;
+    j1 = pre * r1 * nrm;
+}
+
+// j_nu(x) for a real multipole nu >= 2: from j_v0 and j_v0+1 (v0 = frac(nu))
+// forward to nu when x > nu, else Miller's backward recurrence from
+// nu + 20 + 10 nu^(1/3) down to v0 matched to them (least squares, as for
+// integer orders).  Values below 1e-323 are zero.
+__device__ double jnu_real(double nu, double x)
+{
+    if (!(x > 0.0)) return 0.0;
+    if (nu * log(2.718281828459045 * x / (2.0 * nu)) < -744.0) return 0.0;
+    const int n = (int)floor(nu);
+    const double v0 = nu - n;
+    double j0, j1;
+    jnu_start(v0, x, j0, j1);
+    if (n == 0) return j0;
+    if (x > nu) {
+        double jm = j0, jc = j1, v = v0 + 1.0;
+        for (int k = 1; k < n; k++) {
+            const double jn = (2.0 * v + 1.0) / x * jc - jm;
+            jm = jc;
+            jc = jn;
+            v += 1.0;
+        }
+        return jc;
+    }
+    const int top = n + 20 + (int)(10.0 * cbrt((double)n));
+    double fp = 0.0, f = 1e-200, rec = 0.0, v = v0 + top;
+    for (int k = top; k > 0; k--) {
+        if (k == n) rec = f;
+        const double fm = (2.0 * v + 1.0) / x * f - fp;  // order v - 1
+        fp = f;
+        f = fm;
+        v -= 1.0;
+        if (fabs(f) > 1e200) { f *= 1e-200; fp *= 1e-200; rec *= 1e-200; }
+    }
+    const double mx = fmax(fabs(f), fabs(fp));
+    f /= mx;
+    fp /= mx;
+    return rec * (j0 * f + j1 * fp) / ((f * f + fp * fp) * mx);
+}
+
 template <int ROWS>
 __global__ void __launch_bounds__(kThreads)
 k_basis_gemm(const double *__restrict__ A, const double *__restrict__ kq, int Nk, int N,
-             const int *__restrict__ ell, int L, int e0, const double *__restrict__ chi,
+             const double *__restrict__ ell, int real_ell, int L, int e0, const double *__restrict__ chi,
              const double *__restrict__ R, int Rn, int Q, double *__restrict__ T)
 {
     extern __shared__ double sm[];
@@ -111,12 +228,16 @@ k_basis_gemm(const double *__restrict__ A, const double *__restrict__ kq, int Nk
     double *Jv = As + kMC * rows3;             // [(1+kRT) kMC][kG]
     double *Bp = Jv + (1 + kRT) * kMC * kG;    // [kMC][kG*kRT]
     __shared__ int lg[kG];
+    __shared__ double lgr[kG];
 
     const int tid = threadIdx.x;
     const int a = blockIdx.y;
     const int r0 = blockIdx.x * kRT;
     const int ng = min(kG, L - e0);
-    if (tid < kG) lg[tid] = (tid < ng) ? ell[e0 + tid] : 0;
+    if (tid < kG) {
+        lgr[tid] = (tid < ng) ? ell[e0 + tid] : 0.0;
+        lg[tid] = (int)lgr[tid];
+    }
     const double chia = chi[a];
     const int rb = tid >> 3, cb = tid & 7;
     double acc[ROWS][kG];
@@ -136,8 +257,12 @@ k_basis_gemm(const double *__restrict__ A, const double *__restrict__ kq, int Nk
             const int r = r0 + side - 1;
             bool ok = mi < mcnt && (side == 0 || r < Rn);
             double dist = (side == 0) ? chia : (ok ? R[r] * chia : 0.0);
-            if (ok) jl_group(kq[m0 + mi] * dist, lg, ng, out);
-            else {
+            if (ok && !real_ell) {
+                jl_group(kq[m0 + mi] * dist, lg, ng, out);
+            } else if (ok) {  // each non-integer multipole has its own recurrence
+#pragma unroll
+                for (int g = 0; g < kG; g++) out[g] = (g < ng) ? jnu_real(lgr[g], kq[m0 + mi] * dist) : 0.0;
+            } else {
 #pragma unroll
                 for (int g = 0; g < kG; g++) out[g] = 0.0;
             }
@@ -189,14 +314,15 @@ __global__ void k_basis_to_f32(const double *__restrict__ T, float *__restrict__
 }
 
 template <int ROWS>
-int launch_gemm_rows(blast_plan *p, const double *A, const double *kq, const int *ell, const double *R,
+int launch_gemm_rows(blast_plan *p, const double *A, const double *kq, const double *ell, const double *R,
                      cudaStream_t s)
 {
     size_t smem = sizeof(double) * ((size_t)kMC * 3 * p->N + (size_t)(1 + kRT) * kMC * kG + (size_t)kMC * kG * kRT);
     BL_CUDA(allow_opt_in_smem(k_basis_gemm<ROWS>, p->device));
     dim3 grid((p->Rn + kRT - 1) / kRT, p->X);
     for (int e0 = 0; e0 < p->L; e0 += kG) {
-        k_basis_gemm<ROWS><<<grid, kThreads, smem, s>>>(A, kq, p->Nk, p->N, ell, p->L, e0, p->d_chi, R,
+        k_basis_gemm<ROWS><<<grid, kThreads, smem, s>>>(A, kq, p->Nk, p->N, ell, p->real_ell ? 1 : 0, p->L, e0,
+                                                        p->d_chi, R,
                                                         p->Rn, p->Q, p->T64);
         BL_CUDA(cudaGetLastError());
     }
@@ -210,19 +336,19 @@ int launch_basis(blast_plan *p, cudaStream_t s)
     const int rows3 = 3 * p->N;
     if (rows3 > 32 * 12) return BLAST_EINVAL;  // n_cheb <= 128 (ROWS <= 12)
     double *kq = nullptr, *wq = nullptr, *A = nullptr, *R = nullptr;
-    int *ell = nullptr;
+    double *ell = nullptr;
     int rc = BLAST_OK;
     size_t nA = (size_t)p->Nk * rows3;
     if (cudaMalloc(&kq, sizeof(double) * p->Nk) || cudaMalloc(&wq, sizeof(double) * p->Nk) ||
         cudaMalloc(&A, sizeof(double) * nA) || cudaMalloc(&R, sizeof(double) * p->Rn) ||
-        cudaMalloc(&ell, sizeof(int) * p->L)) {
+        cudaMalloc(&ell, sizeof(double) * p->L)) {
         cudaGetLastError();
         rc = BLAST_ENOMEM;
     }
     if (!rc && (cudaMemcpyAsync(kq, p->kq.data(), sizeof(double) * p->Nk, cudaMemcpyHostToDevice, s) ||
                 cudaMemcpyAsync(wq, p->wq.data(), sizeof(double) * p->Nk, cudaMemcpyHostToDevice, s) ||
                 cudaMemcpyAsync(R, p->R.data(), sizeof(double) * p->Rn, cudaMemcpyHostToDevice, s) ||
-                cudaMemcpyAsync(ell, p->ell.data(), sizeof(int) * p->L, cudaMemcpyHostToDevice, s)))
+                cudaMemcpyAsync(ell, p->ell.data(), sizeof(double) * p->L, cudaMemcpyHostToDevice, s)))
         rc = BLAST_EDEVICE;
     if (!rc) {
         k_basis_A<<<(p->Nk + 255) / 256, 256, 0, s>>>(kq, wq, p->Nk, p->N, p->kmap, p->k_min, p->k_max, A);
