@@ -84,6 +84,25 @@ def test_tc_two_ragged_cosmology_tiles(tc_case):
     assert np.array_equal(outs[0], outs[125]) and np.array_equal(outs[4], outs[129])
 
 
+def test_tc_host_input_tiles_equal_device_input_batch(tc_case):
+    """A batch of three cosmology tiles with host inputs (read in place over the
+    host link) gives the bits of the same batch with device inputs."""
+    import torch
+    spec, g, T, plan = tc_case
+    base = [synth.config_request("tc", g.chi, g.R, i) for i in range(9)]
+    rqs = [base[i % 9] for i in range(300)]
+    host = plan.cl_batch(rqs, bl.BLAST_BF16S)
+    fields = ["kern_chi", "kern_Rchi", "growth_chi", "growth_Rchi", "k_tab", "p_tab"]
+    dev = [{f: torch.from_numpy(np.ascontiguousarray(getattr(rq, f))).cuda() for f in fields} for rq in base]
+    reqs = [plan.request(base[i % 9], device_arrays=dev[i % 9]) for i in range(300)]
+    outs = [torch.empty(h.shape, dtype=torch.float64, device="cuda") for h in host]
+    assert bl.blast_cl_batch(plan.h, reqs, bl.BLAST_BF16S, [o.data_ptr() for o in outs], 1,
+                             torch.cuda.current_stream().cuda_stream) == bl.BLAST_OK
+    torch.cuda.synchronize()
+    for h, o in zip(host, outs):
+        assert np.array_equal(h, o.cpu().numpy())
+
+
 @pytest.mark.parametrize("n", [1, 31, 33, 64, 97])
 def test_tc_partial_tiles_equal_full_batch(tc_case, n):
     """Batches that fill only some 32-lane quadrants of a tile (whose epilogue
