@@ -376,7 +376,8 @@ int blast_graph_destroy(blast_graph *graph);
 #define BLAST_K_CLASSES 5
 
 /* Per-kernel device time.  While enabled, every evaluation call brackets each
- * of its kernel launches with CUDA events recorded on the call's stream.
+ * of its kernel launches with CUDA events recorded on the stream the kernel
+ * runs on (the call's stream, or the plan's side stream of the fit).
  * blast_profile_read waits for those events and returns, for one kernel class,
  * the summed device milliseconds and the launch count since the last reset
  * (launches are counted whether or not timing is enabled). */

@@ -93,3 +93,26 @@ def test_integer_values_as_real_multipoles_give_the_integer_plan():
     finally:
         p_int.close()
         p_real.close()
+
+
+def test_real_ells_in_the_symmetrised_form():
+    """Both plan options at once: non-integer multipoles on the symmetrised
+    chi-R form, FP64 against the oracle's symmetrised form at real ells."""
+    spec = dataclasses.replace(synth.plan_spec("tiny"), ells=REAL["tiny"], r_form=1)
+    g = orc.Grid(spec.ells, spec.n_chi, spec.chi_min, spec.chi_max, spec.n_R, spec.R_min, spec.R_max,
+                 spec.n_cheb, spec.k_min, spec.k_max, spec.n_kquad, spec.k_map, r_form=1)
+    To = g.basis()
+    plan = bl.Plan(spec)
+    try:
+        plan.precompute(bl.BASIS_ALL)
+        Tg = plan.basis()
+        scale = np.abs(To).max(axis=-1, keepdims=True)
+        scale[scale == 0] = 1.0
+        assert np.max(np.abs(Tg - To) / scale) < 1e-11
+        rq = synth.config_request("tiny", g.chi, g.R, 44)
+        a = g.fit(rq.k_tab, rq.p_tab)
+        Co = g.cl(To, a, rq.n_clust, rq.n_lens, rq.kern_chi, rq.kern_Rchi, rq.growth_chi, rq.growth_Rchi)
+        C = plan.cl(rq, bl.BLAST_FP64)
+        assert np.max(eij(C, Co, rq.n_clust, rq.n_lens)) < 1e-10
+    finally:
+        plan.close()
